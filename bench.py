@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark of the coupled D3Q19 LB + polymer MD step on GB300.
+
+Workload (default): the paper-shaped translocation box 256 x 128 x 128, wall at
+x = 128 with a 5 x 5 pore, one 400-bead chain (seeded self-avoiding walk),
+tau = 1, FP32 population storage.  One "step" is one coupled LB step: bead
+gather, M = 5 MD substeps, the D3Q19 stream-collide of the whole box and the
+spread of the bead impulses.  Metric: MLUPS (all box nodes x steps / s).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 the script runs under torch.distributed (one rank per GPU); every
+rank steps its own independent realisation (different seed) -- weak scaling
+with no collective on the data path; the timed region is bracketed by
+barriers and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import seeded_inputs as si  # noqa: E402
+
+BYTES_PER_NODE = {"f32": 152, "f16": 76, "bf16": 76}  # 19 loads + 19 stores
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(seed: int, storage: str):
+    p = si.paper_translocation(seed)
+    p["storage"] = storage
+    return p
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def shard_seed(base: int, rank: int) -> int:
+    """Seed of the independent realisation a rank steps (weak scaling)."""
+    return base + 7919 * rank
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index: int, period_ms: int = 100):
+        self.index, self.period_ms = index, period_ms
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", str(self.period_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(p, pos, seconds: float):
+    """The FP64 oracle, as it stands, on the host cores: full box, as many LB
+    steps as fit in about `seconds` (at least one)."""
+    import oracle
+
+    cores = oracle.max_threads()
+    op = {k: v for k, v in p.items() if k not in ("storage", "init_tg_amp")}
+    sim = oracle.OracleSim(op, init_pos=pos)
+    t0 = time.perf_counter()
+    sim.step(1)
+    t1 = time.perf_counter()
+    per = t1 - t0
+    n = max(1, min(50, int(seconds / max(per, 1e-6)) - 1))
+    t0 = time.perf_counter()
+    sim.step(n)
+    dt = time.perf_counter() - t0
+    V = p["nx"] * p["ny"] * p["nz"]
+    return {"value": V * n / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{n} coupled LB steps of the {p['nx']}x{p['ny']}x{p['nz']} box with "
+                      f"{p['n_beads']} beads after 1 warm-up step (FP64, OpenMP)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    p = workload(0, args.storage)
+    pos = si.saw_chain(p, 0)
+    import oracle
+
+    op = {k: v for k, v in p.items() if k not in ("storage", "init_tg_amp")}
+    sim = oracle.OracleSim(op, init_pos=pos)
+    sim.step(min(args.warmup, 1))
+    budget = 90.0
+    t0 = time.perf_counter()
+    done = 0
+    while done < args.steps and (time.perf_counter() - t0) < budget:
+        sim.step(1)
+        done += 1
+    dt = time.perf_counter() - t0
+    V = p["nx"] * p["ny"] * p["nz"]
+    value = V * done / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "coupled D3Q19 MLUPS", "value": value, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": done, "warmup": min(args.warmup, 1),
+        "ms_per_step": 1e3 * dt / max(done, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "translocation 256x128x128, wall x=128, 5x5 pore, N=400 beads, tau=1",
+                   "storage": "f64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.max_threads(),
+                         "kind": "oracle",
+                         "sample": f"{done} of {args.steps} requested steps (time cap {budget:.0f} s) "
+                                   "of the full box, FP64 oracle with OpenMP"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_0710_1272_gb300 as lb
+
+    p = workload(shard_seed(0, rank), args.storage)
+    pos = si.saw_chain(p, shard_seed(0, rank))
+    V = p["nx"] * p["ny"] * p["nz"]
+    stream = torch.cuda.Stream()
+    sim = lb.Simulation(p, init_pos=pos, stream=stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # -- warm-up (captures the step graphs) ------------------------------------
+    sim.step(args.warmup)
+    barrier()
+
+    # -- timed region: graph replays of the coupled step -------------------------
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        barrier()
+        # second region of the same length with the stream-collide launches
+        # bracketed by events on their own stream (direct launches, no graph)
+        sim.set_kernel_timing(True)
+        barrier()
+        ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev2.record(stream)
+        sim.step(args.steps)
+        ev3.record(stream)
+        barrier()
+        lb_ms, lb_n = sim.lb_kernel_time()
+        sim.set_kernel_timing(False)
+    ms = ev0.elapsed_time(ev1)
+    ms_direct = ev2.elapsed_time(ev3)
+    if dist is not None:
+        t = torch.tensor([ms, ms_direct], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_direct = t.tolist()
+    st = sim.status()
+
+    # -- end to end through the public API with host buffers ------------------
+    e2e_steps = args.e2e_steps
+    N = p["n_beads"]
+    pos_h = np.empty((N, 3))
+    vel_h = np.empty((N, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lb.lbmd_step(sim.ctx, 1)
+        lb.lbmd_read_beads(sim.ctx, pos_h.ctypes.data, vel_h.ctypes.data, 0)
+        lb.lbmd_status(sim.ctx)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = t.item()
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    value = world * V * args.steps / (ms / 1e3) / 1e6
+    peak, peak_kind = measured_peak_hbm()
+    solid = si.solid_mask(p)
+    fluid = int(V - solid.sum())
+    bytes_per_launch = BYTES_PER_NODE[args.storage] * fluid
+    lb_avg_s = lb_ms / 1e3 / max(lb_n, 1)
+    achieved = bytes_per_launch / lb_avg_s / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "lb_stream_collide_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as f:
+                tj = json.load(f)
+            if tj.get("storage") == args.storage and tj.get("kernel_rev") == kernel_rev():
+                traffic = tj["bytes_per_launch"]
+        except (OSError, ValueError, KeyError):
+            traffic = None
+    clocks = clk.summary()
+    line = {
+        "metric": "coupled D3Q19 MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": "translocation 256x128x128, wall x=128, 5x5 pore, N=400 beads, tau=1",
+                   "storage": args.storage, "seed": shard_seed(0, rank), "parallelism":
+                   "independent realisation per GPU" if world > 1 else "1 GPU",
+                   "l2": "no flush: populations 637.5 MB/step (fp32) > 129 MB L2"},
+        "coupled_steps_per_s": world * args.steps / (ms / 1e3),
+        "value_direct_launch": world * V * args.steps / (ms_direct / 1e3) / 1e6,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_stream_collide", "peak_source": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "avg_launch_ms": lb_avg_s * 1e3, "launches_timed": lb_n},
+        "e2e": {"value": world * V * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": N * 48 + 24,
+                "api": "lbmd_step(1) + lbmd_read_beads(host) + lbmd_status per step"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+        "status": st,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, pos, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def kernel_rev() -> str:
+    """Hash of the stream-collide sources: a stored DRAM-traffic figure is only
+    reported while the kernel it was measured on is unchanged."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in ("lb_kernels.cu", "lb_pull.cuh", "lbmd_common.cuh"):
+        with open(os.path.join(ROOT, "paper_0710_1272_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

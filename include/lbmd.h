@@ -1,0 +1,205 @@
+/*
+ * lbmd.h -- C ABI of the GB300 (sm_103a) coupled lattice-Boltzmann / polymer
+ * molecular-dynamics step of Fyta, Melchionna, Kaxiras and Succi,
+ * "Coupling Lattice Boltzmann with Atomistic Dynamics for the multiscale
+ * simulation of nano-biological flows" (arXiv:0710.1272).
+ *
+ * One call of lbmd_step advances the coupled system by one LB time step
+ * (Delta t = 1) following the four-stage scheme of Sec. II:
+ *   (1) interpolate the fluid velocity u(x) to the beads,
+ *   (2) run M MD substeps (Delta t_MD = 1/M) with u frozen,
+ *   (3) extrapolate the bead friction + random forces back to the grid,
+ *   (4) advance the D3Q19 populations by one stream-collide (Eq. 5).
+ *
+ * Conventions shared by every entry point:
+ *  - All functions return an int status: LBMD_OK (0) or a negative LBMD_E*
+ *    code.  A CUDA failure inside a context is sticky: later calls on that
+ *    context return LBMD_ECUDA until it is destroyed.
+ *  - The library never allocates device memory.  The caller passes one device
+ *    workspace (size from lbmd_workspace_size, 256-byte aligned) and a CUDA
+ *    stream; every kernel runs on that stream or on a private second stream
+ *    that is forked from and joined back into it.  The caller owns the
+ *    workspace, the stream and every output buffer.
+ *  - Work is asynchronous on the stream unless a function says it
+ *    synchronises.
+ *  - Lattice arrays are structure-of-arrays, x fastest: a scalar field is
+ *    [z][y][x] (V = nx*ny*nz entries); a vector field is [3][z][y][x]; the
+ *    populations are [19][z][y][x].
+ *  - D3Q19 population order: 0 rest; 1/2 = +x/-x; 3/4 = +y/-y; 5/6 = +z/-z;
+ *    7/8 = (+1,+1,0)/(-1,-1,0); 9/10 = (+1,-1,0)/(-1,+1,0);
+ *    11/12 = (+1,0,+1)/(-1,0,-1); 13/14 = (+1,0,-1)/(-1,0,+1);
+ *    15/16 = (0,+1,+1)/(0,-1,-1); 17/18 = (0,+1,-1)/(0,-1,+1).
+ *  - Not thread-safe per context; separate contexts are independent.
+ */
+#ifndef LBMD_H
+#define LBMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LBMD_OK 0
+#define LBMD_EINVAL (-1)       /* a parameter or argument is out of range    */
+#define LBMD_ESIZE (-2)        /* workspace too small or misaligned          */
+#define LBMD_ECUDA (-3)        /* a CUDA runtime call failed (sticky)        */
+#define LBMD_EUNSUPPORTED (-4) /* valid for the method, not built here       */
+
+/* ---- per-chain state word (lbmd_status) -------------------------------- */
+#define LBMD_RUNNING 0
+#define LBMD_TRANSLOCATED 1 /* every bead on the trans side x < wall_x      */
+#define LBMD_RETRACTED 2    /* crossed, then all beads back past the pore   */
+#define LBMD_NAN 3          /* a bead position or velocity is not finite    */
+#define LBMD_SHAKE_FAIL 4   /* the constraint solve did not converge        */
+
+/* ---- option values ----------------------------------------------------- */
+#define LBMD_STORE_F32 0  /* populations stored as float deviations        */
+#define LBMD_STORE_F16 1  /* ... as IEEE half deviations f - w_p rho0      */
+#define LBMD_STORE_BF16 2 /* ... as bfloat16 deviations                    */
+#define LBMD_FORCING_PAPER 0 /* first-order source (w_p/c_s^2) c_p.F, Eq. 10 */
+#define LBMD_FORCING_GUO 1   /* Guo second-order forcing for the body force  */
+#define LBMD_COUPLING_TRILINEAR 0 /* 8-node trilinear gather / spread        */
+#define LBMD_COUPLING_NGP 1       /* nearest grid point (the paper's choice) */
+
+/* Largest chain one context accepts (one GPU thread block per chain). */
+#define LBMD_MAX_BEADS 1024
+
+/*
+ * Problem statement of Sec. III plus the method parameters of Sec. II.
+ * All lengths and times are in lattice units (Delta x = Delta t = 1).
+ * Host pointers in this struct are read during lbmd_create only.
+ */
+typedef struct lbmd_params {
+  int32_t nx, ny, nz;          /* box; periodic in every direction          */
+  int32_t wall_x;              /* first x-layer of the wall; -1: no wall    */
+  int32_t wall_thickness;      /* wall layers (paper: 1)                    */
+  int32_t pore_d;              /* side of the square pore (paper: 3); 0: closed */
+  int32_t pore_y0, pore_z0;    /* lowest pore node; -1: centred, (n - d)/2  */
+  int32_t y_walls;             /* 1: solid rows y = 0 and y = ny-1          */
+  int32_t storage;             /* LBMD_STORE_*                              */
+  int32_t forcing;             /* LBMD_FORCING_*                            */
+  int32_t coupling;            /* LBMD_COUPLING_*                           */
+  int32_t n_beads;             /* 0 .. LBMD_MAX_BEADS                       */
+  int32_t md_substeps;         /* M of Sec. II (paper: 5), 1 .. 255         */
+  int32_t n_constraints;       /* -1: linear chain of n_beads-1 bonds of
+                                  bond_length; 0: free beads; >0: the bonds
+                                  below (must form the linear chain k, k+1) */
+  int32_t shake_max_iter;      /* Newton iterations per constraint solve    */
+  double tau;                  /* BGK relaxation time, nu = (tau - 1/2)/3   */
+  double rho0;                 /* reference density (paper: 1)              */
+  double body_force[3];        /* uniform force density g                   */
+  double bead_mass;            /* m (paper: unspecified; 1)                 */
+  double gamma;                /* friction coefficient of Eq. 4 (paper 0.1) */
+  double kT;                   /* 1/beta (paper: 1e-4)                      */
+  double lj_sigma, lj_eps;     /* Eq. 2, truncated at 2^(1/6) sigma         */
+  double kappa_phi;            /* bending stiffness of Eq. 3                */
+  double f_drive;              /* pulling force in the pore (paper: 0.02)   */
+  double bond_length;          /* b (paper: 1.2) for n_constraints == -1    */
+  double shake_tol;            /* max |d^2 - b^2| / b^2 accepted            */
+  double init_tg_amp;          /* Taylor-Green amplitude if init_u == NULL  */
+  uint64_t seed;               /* Philox key of the bead noise              */
+  const int32_t *bond_i;       /* host, n_constraints entries               */
+  const int32_t *bond_j;
+  const double *bond_len;
+  const double *init_pos;      /* host, 3*n_beads, unwrapped [i][xyz]        */
+  const double *init_vel;      /* host, 3*n_beads or NULL (zero)             */
+  const double *init_rho;      /* host, V or NULL (rho0)                     */
+  const double *init_u;        /* host, 3*V SoA or NULL                      */
+} lbmd_params;
+
+typedef struct lbmd_ctx lbmd_ctx; /* opaque */
+
+/*
+ * Bytes of device workspace lbmd_create needs for these parameters (two
+ * population buffers, the solid bitfield, bead state and read-out staging).
+ * Validates the parameters; no CUDA call, callable without a GPU.
+ * Errors: LBMD_EINVAL (bad parameter, message in lbmd_last_message).
+ */
+int lbmd_workspace_size(const lbmd_params *params, size_t *bytes);
+
+/*
+ * Build the geometry of Sec. III (wall at x = wall_x, centred d x d pore,
+ * optional y-walls), the equilibrium populations f = f_eq(rho, u) of the
+ * initial fields, and the bead state; everything is written into the caller's
+ * workspace on `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+ * The call synchronises the stream before it returns.
+ * Errors: LBMD_EINVAL, LBMD_ESIZE (bytes too small or workspace not 256-byte
+ * aligned), LBMD_EUNSUPPORTED (constraint topology other than a linear
+ * chain), LBMD_ECUDA.  On error *out is NULL and nothing is leaked.
+ */
+int lbmd_create(const lbmd_params *params, void *dev_workspace, size_t bytes,
+                void *cuda_stream, lbmd_ctx **out);
+
+/*
+ * Advance n_steps coupled LB steps (Sec. II scheme above), asynchronously on
+ * the context's stream.  The steps replay a CUDA graph captured at the first
+ * call (disabled while kernel timing is on).  n_steps >= 0.
+ * Errors: LBMD_EINVAL, LBMD_ECUDA.
+ */
+int lbmd_step(lbmd_ctx *ctx, int64_t n_steps);
+
+/*
+ * Density rho (V floats) and velocity u = sum_p f_p c_p / rho (3*V floats,
+ * [3][z][y][x]) of the current pre-collision populations (Eqs. 7-8; with Guo
+ * forcing u carries the +g/(2 rho) shift).  Solid nodes read 0.
+ * dst_is_device: 1 if rho/u are device pointers (stream-ordered, async);
+ * 0 for host memory (the call synchronises).  Either pointer may be NULL.
+ */
+int lbmd_read_fields(lbmd_ctx *ctx, float *rho, float *u, int dst_is_device);
+
+/*
+ * The 19 pre-collision populations f_p(x, t) (19*V floats, [19][z][y][x]),
+ * i.e. after streaming and bounce-back, before the next collision.  Solid
+ * nodes read 0.  dst_is_device as above.
+ */
+int lbmd_read_populations(lbmd_ctx *ctx, float *f, int dst_is_device);
+
+/*
+ * Bead positions (unwrapped, 3*n_beads doubles [i][xyz]) and velocities.
+ * dst_is_device as above.  Either pointer may be NULL.
+ */
+int lbmd_read_beads(lbmd_ctx *ctx, double *pos, double *vel, int dst_is_device);
+
+/*
+ * Of the last step: the fluid velocity interpolated at each bead, u_i, and the
+ * impulse J_i = sum over substeps of Delta t_MD (F_drag + F_r) that was handed
+ * to the fluid (with the opposite sign).  3*n_beads doubles each.
+ */
+int lbmd_read_bead_aux(lbmd_ctx *ctx, double *u_i, double *impulse, int dst_is_device);
+
+/*
+ * Step counter, number of translocated beads N_T (x < wall_x, Sec. III), the
+ * chain state word (LBMD_RUNNING, ...) and the first step with N_T = N (-1 if
+ * none).  Synchronises the stream.  Any pointer may be NULL.
+ */
+int lbmd_status(lbmd_ctx *ctx, int64_t *step, int32_t *n_trans, int32_t *state,
+                int64_t *t_transloc);
+
+/*
+ * Kernel timing for benchmarks: while enabled, lbmd_step launches kernels
+ * directly (no graph) and brackets every stream-collide launch with CUDA
+ * events on its stream.  lbmd_lb_kernel_time synchronises and returns the
+ * summed duration (ms) and count of those launches since timing was enabled.
+ */
+int lbmd_set_kernel_timing(lbmd_ctx *ctx, int enable);
+int lbmd_lb_kernel_time(lbmd_ctx *ctx, double *total_ms, int64_t *launches);
+
+/* Release the context's host resources (not the caller's workspace). */
+int lbmd_destroy(lbmd_ctx *ctx);
+
+/* Static description of a status code. */
+const char *lbmd_strerror(int status);
+
+/* Thread-local text of the last LBMD_EINVAL / LBMD_ECUDA cause. */
+const char *lbmd_last_message(void);
+
+/* ABI version: (major << 16) | minor. */
+int lbmd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBMD_H */

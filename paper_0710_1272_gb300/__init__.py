@@ -1,0 +1,14 @@
+"""GB300 (sm_103a) implementation of the coupled lattice-Boltzmann / polymer-MD
+step of Fyta, Melchionna, Kaxiras and Succi (arXiv:0710.1272).
+
+The compute path is the CUDA library ``liblbmd.so`` (sources in ``csrc/``,
+C ABI in ``include/lbmd.h``); :mod:`.lbmd` is its ctypes binding and
+:class:`Simulation` a convenience wrapper that owns a torch device workspace.
+"""
+from .lbmd import (  # noqa: F401
+    COUPLING, FORCING, MAX_BEADS, NAN, RETRACTED, RUNNING, SHAKE_FAIL, STORAGE, TRANSLOCATED,
+    LbmdError, Simulation, full_params, lbmd_create, lbmd_destroy, lbmd_lb_kernel_time,
+    lbmd_read_bead_aux, lbmd_read_beads, lbmd_read_fields, lbmd_read_populations,
+    lbmd_set_kernel_timing, lbmd_status, lbmd_step, lbmd_version, lbmd_workspace_size, load,
+    make_params,
+)

@@ -1,0 +1,288 @@
+// lb_kernels.cu -- D3Q19 BGK stream-collide (Eq. 5 with the Eq. 6 equilibrium
+// and the body-force source), population initialisation and field read-outs.
+//
+// Layout: structure of arrays, h[p][z][y][x] with population stride Vp, every
+// entry the deviation h = f - w_p rho0 in the storage type.  One thread per
+// node; a warp covers 32 consecutive x of one (y, z) row so that every one of
+// the 19 loads and 19 stores of a warp is a contiguous 128-byte (fp32) or
+// 64-byte (16-bit) segment; the loads for c_x = +-1 are shifted by one element
+// and are served from L1/L2 for the neighbouring warp's sector.
+#include "lb_pull.cuh"
+
+namespace lbmd {
+
+constexpr int kRowsPerBlock = 8;  // block = 32 x 8 threads
+
+// Post-collision deviation of every population of one node from its
+// pre-collision deviations (Eq. 5, omega = 1/tau, Delta t = 1):
+//   h*_p = h_p - omega (h_p - heq_p) + S_p,
+//   heq_p = w_p [ (rho - rho0) + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u) ]   (Eq. 6),
+//   paper forcing: S_p = 3 w_p c_p . g;
+//   Guo forcing:   u = (j + g/2)/rho, S_p = (1 - omega/2) w_p [3 (c - u) + 9 (c.u) c] . g.
+template <int FORCING>
+__device__ __forceinline__ void collide19(float h[kQ], const LbPhys &ph) {
+  float drho, jx, jy, jz;
+  moments19(h, drho, jx, jy, jz);
+  const float rho = ph.rho0 + drho;
+  const float inv = 1.0f / rho;
+  float ux, uy, uz;
+  if (FORCING == LBMD_FORCING_GUO) {
+    ux = (jx + 0.5f * ph.g[0]) * inv;
+    uy = (jy + 0.5f * ph.g[1]) * inv;
+    uz = (jz + 0.5f * ph.g[2]) * inv;
+  } else {
+    ux = jx * inv;
+    uy = jy * inv;
+    uz = jz * inv;
+  }
+  const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+  const float om = ph.omega;
+  const float gu = ph.g[0] * ux + ph.g[1] * uy + ph.g[2] * uz;
+  const float kguo = 1.0f - 0.5f * om;
+#pragma unroll
+  for (int p = 0; p < kQ; ++p) {
+    const float cu = cx(p) * ux + cy(p) * uy + cz(p) * uz;
+    const float heq = wq(p) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - usq15));
+    const float cg = cx(p) * ph.g[0] + cy(p) * ph.g[1] + cz(p) * ph.g[2];
+    float src;
+    if (FORCING == LBMD_FORCING_GUO)
+      src = kguo * wq(p) * (3.0f * (cg - gu) + 9.0f * cu * cg);
+    else
+      src = 3.0f * wq(p) * cg;
+    h[p] = h[p] - om * (h[p] - heq) + src;
+  }
+}
+
+template <int S, int FORCING>
+__global__ void __launch_bounds__(32 * kRowsPerBlock)
+    k_stream_collide(LbGeom g, LbPhys ph, const typename Store<S>::T *__restrict__ src,
+                     typename Store<S>::T *__restrict__ dst, DevStatus *bump) {
+  using St = Store<S>;
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kRowsPerBlock + threadIdx.y;
+  const int z = blockIdx.z;
+  if (bump != nullptr && x == 0 && y == 0 && z == 0) bump->step += 1;
+  if (x >= g.nx || y >= g.ny) return;
+  const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
+  float h[kQ];
+  if (tile_is_near(g, x, y, z)) {
+    if (solid_at(g.solid, g.ntx, g.ny, x, y, z)) return;
+    pull19<S, true>(g, src, x, y, z, h);
+  } else {
+    pull19<S, false>(g, src, x, y, z, h);
+  }
+  collide19<FORCING>(h, ph);
+  const size_t Vp = (size_t)g.Vp;
+#pragma unroll
+  for (int p = 0; p < kQ; ++p) St::store(dst + (size_t)p * Vp + self, h[p]);
+}
+
+template <int S>
+static cudaError_t lb_launch(const LbGeom &g, const LbPhys &ph, const void *src, void *dst,
+                             DevStatus *bump, cudaStream_t s) {
+  using T = typename Store<S>::T;
+  dim3 block(32, kRowsPerBlock);
+  dim3 grid(g.ntx, (g.ny + kRowsPerBlock - 1) / kRowsPerBlock, g.nz);
+  if (ph.forcing == LBMD_FORCING_GUO)
+    k_stream_collide<S, LBMD_FORCING_GUO><<<grid, block, 0, s>>>(g, ph, (const T *)src, (T *)dst, bump);
+  else
+    k_stream_collide<S, LBMD_FORCING_PAPER><<<grid, block, 0, s>>>(g, ph, (const T *)src, (T *)dst, bump);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lb_stream_collide(int storage, const LbGeom &g, const LbPhys &ph,
+                                     const void *src, void *dst, DevStatus *bump,
+                                     cudaStream_t s) {
+  switch (storage) {
+    case LBMD_STORE_F32: return lb_launch<LBMD_STORE_F32>(g, ph, src, dst, bump, s);
+    case LBMD_STORE_F16: return lb_launch<LBMD_STORE_F16>(g, ph, src, dst, bump, s);
+    case LBMD_STORE_BF16: return lb_launch<LBMD_STORE_BF16>(g, ph, src, dst, bump, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation: the pre-collision state f(x, 0) = f_eq(rho(x), u(x)) must be
+// what the first pull produces, so the stored post-collision buffer holds
+//   h*_q(y) = f_eq,q(y + c_q) - w_q rho0     if y + c_q is fluid,
+//   h*_q(y) = f_eq,opp(q)(y) - w_q rho0      otherwise (bounce-back source),
+// at fluid nodes y, and zero at solid nodes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void init_fields_at(int x, int y, int z, const LbGeom &g, float rho0,
+                                               const float *rho, const float *u, float tg_amp,
+                                               float &r, float &ux, float &uy, float &uz) {
+  const size_t c = ((size_t)z * g.ny + y) * g.nx + x;
+  r = rho ? rho[c] : rho0;
+  if (u) {
+    ux = u[c];
+    uy = u[(size_t)g.V + c];
+    uz = u[2 * (size_t)g.V + c];
+  } else if (tg_amp != 0.f) {
+    float sx, cxv, sy, cyv;
+    sincospif(2.0f * (float)x / (float)g.nx, &sx, &cxv);
+    sincospif(2.0f * (float)y / (float)g.ny, &sy, &cyv);
+    ux = tg_amp * sx * cyv;
+    uy = -tg_amp * cxv * sy;
+    uz = 0.f;
+  } else {
+    ux = uy = uz = 0.f;
+  }
+}
+
+__device__ __forceinline__ float feq_dev(int p, float r, float rho0, float ux, float uy, float uz) {
+  const float cu = cx(p) * ux + cy(p) * uy + cz(p) * uz;
+  const float usq = ux * ux + uy * uy + uz * uz;
+  return wq(p) * ((r - rho0) + r * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
+}
+
+template <int S>
+__global__ void k_init(LbGeom g, float rho0, const float *rho, const float *u, float tg_amp,
+                       typename Store<S>::T *__restrict__ dst) {
+  using St = Store<S>;
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kRowsPerBlock + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
+  const size_t Vp = (size_t)g.Vp;
+  if (solid_at(g.solid, g.ntx, g.ny, x, y, z)) {
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) St::store(dst + q * Vp + self, 0.f);
+    return;
+  }
+  float r0, ux0, uy0, uz0;
+  init_fields_at(x, y, z, g, rho0, rho, u, tg_amp, r0, ux0, uy0, uz0);
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int tx = wrapi(x + cx(q), g.nx), ty = wrapi(y + cy(q), g.ny), tz = wrapi(z + cz(q), g.nz);
+    float v;
+    if (q != 0 && !solid_at(g.solid, g.ntx, g.ny, tx, ty, tz)) {
+      float r, ux, uy, uz;
+      init_fields_at(tx, ty, tz, g, rho0, rho, u, tg_amp, r, ux, uy, uz);
+      v = feq_dev(q, r, rho0, ux, uy, uz);
+    } else if (q == 0) {
+      v = feq_dev(0, r0, rho0, ux0, uy0, uz0);
+    } else {
+      v = feq_dev(opp(q), r0, rho0, ux0, uy0, uz0);
+    }
+    St::store(dst + q * Vp + self, v);
+  }
+}
+
+cudaError_t launch_init_populations(int storage, const LbGeom &g, float rho0, const float *rho,
+                                    const float *u, float tg_amp, void *dst, cudaStream_t s) {
+  dim3 block(32, kRowsPerBlock);
+  dim3 grid(g.ntx, (g.ny + kRowsPerBlock - 1) / kRowsPerBlock, g.nz);
+  switch (storage) {
+    case LBMD_STORE_F32:
+      k_init<LBMD_STORE_F32><<<grid, block, 0, s>>>(g, rho0, rho, u, tg_amp, (float *)dst);
+      break;
+    case LBMD_STORE_F16:
+      k_init<LBMD_STORE_F16><<<grid, block, 0, s>>>(g, rho0, rho, u, tg_amp, (__half *)dst);
+      break;
+    case LBMD_STORE_BF16:
+      k_init<LBMD_STORE_BF16><<<grid, block, 0, s>>>(g, rho0, rho, u, tg_amp, (__nv_bfloat16 *)dst);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Read-outs over the z-slab [z0, z0 + nzc): moments (Eqs. 7-8) and the pulled
+// pre-collision populations.  Solid nodes read zero.
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void k_read_moments(LbGeom g, LbPhys ph, const typename Store<S>::T *__restrict__ src,
+                               int z0, float *rho, float *u, long long ustride) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kRowsPerBlock + threadIdx.y;
+  const int z = z0 + blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  const size_t o = ((size_t)blockIdx.z * g.ny + y) * g.nx + x;
+  if (solid_at(g.solid, g.ntx, g.ny, x, y, z)) {
+    if (rho) rho[o] = 0.f;
+    if (u) u[o] = u[ustride + o] = u[2 * ustride + o] = 0.f;
+    return;
+  }
+  float h[kQ];
+  pull19<S, true>(g, src, x, y, z, h);
+  float drho, jx, jy, jz;
+  moments19(h, drho, jx, jy, jz);
+  const float r = ph.rho0 + drho;
+  if (ph.forcing == LBMD_FORCING_GUO) {
+    jx += 0.5f * ph.g[0];
+    jy += 0.5f * ph.g[1];
+    jz += 0.5f * ph.g[2];
+  }
+  if (rho) rho[o] = r;
+  if (u) {
+    u[o] = jx / r;
+    u[ustride + o] = jy / r;
+    u[2 * ustride + o] = jz / r;
+  }
+}
+
+template <int S>
+__global__ void k_read_pulled(LbGeom g, float rho0, const typename Store<S>::T *__restrict__ src,
+                              int z0, float *f, long long fstride) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kRowsPerBlock + threadIdx.y;
+  const int z = z0 + blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  const size_t o = ((size_t)blockIdx.z * g.ny + y) * g.nx + x;
+  if (solid_at(g.solid, g.ntx, g.ny, x, y, z)) {
+#pragma unroll
+    for (int p = 0; p < kQ; ++p) f[p * fstride + o] = 0.f;
+    return;
+  }
+  float h[kQ];
+  pull19<S, true>(g, src, x, y, z, h);
+#pragma unroll
+  for (int p = 0; p < kQ; ++p) f[p * fstride + o] = wq(p) * rho0 + h[p];
+}
+
+cudaError_t launch_read_moments(int storage, const LbGeom &g, const LbPhys &ph, const void *src,
+                                long long z0, long long nzc, float *rho, float *u,
+                                long long ustride, cudaStream_t s) {
+  dim3 block(32, kRowsPerBlock);
+  dim3 grid(g.ntx, (g.ny + kRowsPerBlock - 1) / kRowsPerBlock, (unsigned)nzc);
+  switch (storage) {
+    case LBMD_STORE_F32:
+      k_read_moments<LBMD_STORE_F32><<<grid, block, 0, s>>>(g, ph, (const float *)src, (int)z0, rho, u, ustride);
+      break;
+    case LBMD_STORE_F16:
+      k_read_moments<LBMD_STORE_F16><<<grid, block, 0, s>>>(g, ph, (const __half *)src, (int)z0, rho, u, ustride);
+      break;
+    case LBMD_STORE_BF16:
+      k_read_moments<LBMD_STORE_BF16><<<grid, block, 0, s>>>(g, ph, (const __nv_bfloat16 *)src, (int)z0, rho, u, ustride);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_read_pulled(int storage, const LbGeom &g, float rho0, const void *src,
+                               long long z0, long long nzc, float *f, long long fstride,
+                               cudaStream_t s) {
+  dim3 block(32, kRowsPerBlock);
+  dim3 grid(g.ntx, (g.ny + kRowsPerBlock - 1) / kRowsPerBlock, (unsigned)nzc);
+  switch (storage) {
+    case LBMD_STORE_F32:
+      k_read_pulled<LBMD_STORE_F32><<<grid, block, 0, s>>>(g, rho0, (const float *)src, (int)z0, f, fstride);
+      break;
+    case LBMD_STORE_F16:
+      k_read_pulled<LBMD_STORE_F16><<<grid, block, 0, s>>>(g, rho0, (const __half *)src, (int)z0, f, fstride);
+      break;
+    case LBMD_STORE_BF16:
+      k_read_pulled<LBMD_STORE_BF16><<<grid, block, 0, s>>>(g, rho0, (const __nv_bfloat16 *)src, (int)z0, f, fstride);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lbmd

@@ -1,0 +1,58 @@
+// lb_pull.cuh -- pull streaming with halfway bounce-back, shared by the
+// stream-collide kernel, the read-out kernels and the bead gather.
+#pragma once
+
+#include "lbmd_common.cuh"
+
+namespace lbmd {
+
+// Pre-collision deviations h_p(x, t+1) of node (x, y, z) from the
+// post-collision buffer `src` (Eq. 5 free streaming, pull form):
+//   h_p(x) = h*_p(x - c_p)      if x - c_p is fluid,
+//   h_p(x) = h*_opp(p)(x)       otherwise (the population that left x towards
+//                               the solid node comes back reversed).
+// CHECK = false skips the solid test (tile known to be far from any solid).
+template <int S, bool CHECK>
+__device__ __forceinline__ void pull19(const LbGeom &g, const typename Store<S>::T *__restrict__ src,
+                                       int x, int y, int z, float h[kQ]) {
+  using St = Store<S>;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int xm = wrap_m1(x, nx), xp = wrap_p1(x, nx);
+  const int ym = wrap_m1(y, ny), yp = wrap_p1(y, ny);
+  const int zm = wrap_m1(z, nz), zp = wrap_p1(z, nz);
+  const size_t self = ((size_t)z * ny + y) * nx + x;
+  const size_t Vp = (size_t)g.Vp;
+#pragma unroll
+  for (int p = 0; p < kQ; ++p) {
+    // source node x - c_p
+    const int sx = cx(p) == 1 ? xm : (cx(p) == -1 ? xp : x);
+    const int sy = cy(p) == 1 ? ym : (cy(p) == -1 ? yp : y);
+    const int sz = cz(p) == 1 ? zm : (cz(p) == -1 ? zp : z);
+    const size_t sidx = ((size_t)sz * ny + sy) * nx + sx;
+    if (CHECK && p != 0 && solid_at(g.solid, g.ntx, ny, sx, sy, sz)) {
+      h[p] = St::load(src + (size_t)opp(p) * Vp + self);
+    } else {
+      h[p] = St::load(src + (size_t)p * Vp + sidx);
+    }
+  }
+}
+
+// rho - rho0 and the momentum sum_p h_p c_p (sum_p w_p c_p = 0).
+__device__ __forceinline__ void moments19(const float h[kQ], float &drho, float &jx, float &jy,
+                                          float &jz) {
+  drho = 0.f;
+  jx = jy = jz = 0.f;
+#pragma unroll
+  for (int p = 0; p < kQ; ++p) {
+    drho += h[p];
+    if (cx(p)) jx += cx(p) > 0 ? h[p] : -h[p];
+    if (cy(p)) jy += cy(p) > 0 ? h[p] : -h[p];
+    if (cz(p)) jz += cz(p) > 0 ? h[p] : -h[p];
+  }
+}
+
+__device__ __forceinline__ bool tile_is_near(const LbGeom &g, int x, int y, int z) {
+  return __ldg(&g.tile_near[((size_t)z * g.ny + y) * g.ntx + (x >> 5)]) != 0;
+}
+
+}  // namespace lbmd

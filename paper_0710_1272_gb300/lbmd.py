@@ -1,0 +1,310 @@
+"""Thin ctypes binding of ``include/lbmd.h`` (argument marshalling only).
+
+Every step of the coupled LB / polymer-MD path runs in the CUDA kernels of
+``liblbmd.so``; this module only converts Python values to the C structs and
+pointers, and uses PyTorch for the device workspace and the stream.  There is
+no CPU fallback: if the library is missing or no CUDA device is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBMD_OK, LBMD_EINVAL, LBMD_ESIZE, LBMD_ECUDA, LBMD_EUNSUPPORTED = 0, -1, -2, -3, -4
+RUNNING, TRANSLOCATED, RETRACTED, NAN, SHAKE_FAIL = range(5)
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+FORCING = {"paper": 0, "guo": 1}
+COUPLING = {"trilinear": 0, "ngp": 1}
+MAX_BEADS = 1024
+
+# names of the parameter dict (shared with the oracle's wrapper and the
+# seeded input module) and their defaults
+DEFAULTS = dict(
+    nx=32, ny=16, nz=16,
+    wall_x=-1, wall_thickness=1, pore_d=3, pore_y0=-1, pore_z0=-1, y_walls=0,
+    storage="f32", forcing="paper", coupling="trilinear",
+    n_beads=0, md_substeps=5,
+    tau=1.0, rho0=1.0, body_force=(0.0, 0.0, 0.0),
+    bead_mass=1.0, gamma=0.1, kT=1e-4, lj_sigma=1.8, lj_eps=1.0,
+    kappa_phi=0.0, f_drive=0.02, bond_len=1.2,
+    shake_tol=1e-5, shake_max_iter=12, init_tg_amp=0.0, seed=0,
+)
+IGNORED_KEYS = {"hydrodynamics", "bonds"}  # oracle-only keys
+
+
+class lbmd_params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+        ("wall_x", C.c_int32), ("wall_thickness", C.c_int32),
+        ("pore_d", C.c_int32), ("pore_y0", C.c_int32), ("pore_z0", C.c_int32),
+        ("y_walls", C.c_int32), ("storage", C.c_int32), ("forcing", C.c_int32),
+        ("coupling", C.c_int32), ("n_beads", C.c_int32), ("md_substeps", C.c_int32),
+        ("n_constraints", C.c_int32), ("shake_max_iter", C.c_int32),
+        ("tau", C.c_double), ("rho0", C.c_double), ("body_force", C.c_double * 3),
+        ("bead_mass", C.c_double), ("gamma", C.c_double), ("kT", C.c_double),
+        ("lj_sigma", C.c_double), ("lj_eps", C.c_double), ("kappa_phi", C.c_double),
+        ("f_drive", C.c_double), ("bond_length", C.c_double), ("shake_tol", C.c_double),
+        ("init_tg_amp", C.c_double), ("seed", C.c_uint64),
+        ("bond_i", C.c_void_p), ("bond_j", C.c_void_p), ("bond_len", C.c_void_p),
+        ("init_pos", C.c_void_p), ("init_vel", C.c_void_p),
+        ("init_rho", C.c_void_p), ("init_u", C.c_void_p),
+    ]
+
+
+_lib = None
+
+
+class LbmdError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        L = load()
+        msg = L.lbmd_last_message().decode(errors="replace")
+        super().__init__(f"{where}: {L.lbmd_strerror(code).decode()} ({code}): {msg}")
+        self.code = code
+
+
+def load(build_if_missing: bool = True):
+    """Load liblbmd.so (building it in-tree first if needed); raises if it
+    cannot be built or loaded -- there is no fallback implementation."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library {path} is missing; run paper_0710_1272_gb300.build.build()")
+    L = C.CDLL(path)
+    P = C.c_void_p
+    L.lbmd_workspace_size.argtypes = [C.POINTER(lbmd_params), C.POINTER(C.c_size_t)]
+    L.lbmd_create.argtypes = [C.POINTER(lbmd_params), P, C.c_size_t, P, C.POINTER(P)]
+    L.lbmd_step.argtypes = [P, C.c_int64]
+    L.lbmd_read_fields.argtypes = [P, P, P, C.c_int]
+    L.lbmd_read_populations.argtypes = [P, P, C.c_int]
+    L.lbmd_read_beads.argtypes = [P, P, P, C.c_int]
+    L.lbmd_read_bead_aux.argtypes = [P, P, P, C.c_int]
+    L.lbmd_status.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                              C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
+    L.lbmd_set_kernel_timing.argtypes = [P, C.c_int]
+    L.lbmd_lb_kernel_time.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.lbmd_destroy.argtypes = [P]
+    L.lbmd_strerror.argtypes = [C.c_int]
+    L.lbmd_strerror.restype = C.c_char_p
+    L.lbmd_last_message.restype = C.c_char_p
+    for name in ("lbmd_workspace_size", "lbmd_create", "lbmd_step", "lbmd_read_fields",
+                 "lbmd_read_populations", "lbmd_read_beads", "lbmd_read_bead_aux", "lbmd_status",
+                 "lbmd_set_kernel_timing", "lbmd_lb_kernel_time", "lbmd_destroy", "lbmd_version"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != LBMD_OK:
+        raise LbmdError(rc, where)
+
+
+def full_params(p: dict | None) -> dict:
+    out = dict(DEFAULTS)
+    if p:
+        unknown = set(p) - set(DEFAULTS) - IGNORED_KEYS
+        if unknown:
+            raise KeyError(f"unknown parameter(s): {sorted(unknown)}")
+        out.update({k: v for k, v in p.items() if k not in IGNORED_KEYS})
+    return out
+
+
+def make_params(p: dict, init_pos=None, init_vel=None, init_rho=None, init_u=None, bonds=None):
+    """Fill an lbmd_params struct; returns (struct, keep-alive list)."""
+    p = full_params(p)
+    cp = lbmd_params()
+    for k in ("nx", "ny", "nz", "wall_x", "wall_thickness", "pore_d", "pore_y0", "pore_z0",
+              "y_walls", "n_beads", "md_substeps", "shake_max_iter"):
+        setattr(cp, k, int(p[k]))
+    cp.storage = STORAGE[p["storage"]]
+    cp.forcing = FORCING[p["forcing"]]
+    cp.coupling = COUPLING[p["coupling"]]
+    for k in ("tau", "rho0", "bead_mass", "gamma", "kT", "lj_sigma", "lj_eps", "kappa_phi",
+              "f_drive", "shake_tol", "init_tg_amp"):
+        setattr(cp, k, float(p[k]))
+    cp.bond_length = float(p["bond_len"])
+    for a in range(3):
+        cp.body_force[a] = float(p["body_force"][a])
+    cp.seed = int(p["seed"]) & ((1 << 64) - 1)
+    keep = []
+
+    def arr(x, dtype, shape=None):
+        if x is None:
+            return None
+        a = np.ascontiguousarray(x, dtype=dtype)
+        if shape is not None:
+            a = a.reshape(shape)
+        keep.append(a)
+        return a.ctypes.data
+
+    N = int(p["n_beads"])
+    V = int(p["nx"]) * int(p["ny"]) * int(p["nz"])
+    if bonds is None:
+        cp.n_constraints = -1
+    else:
+        bi, bj, bl = bonds
+        cp.n_constraints = len(bi)
+        cp.bond_i = arr(bi, np.int32)
+        cp.bond_j = arr(bj, np.int32)
+        cp.bond_len = arr(bl, np.float64)
+    cp.init_pos = arr(init_pos, np.float64, (N * 3,))
+    cp.init_vel = arr(init_vel, np.float64, (N * 3,))
+    cp.init_rho = arr(init_rho, np.float64, (V,))
+    cp.init_u = arr(init_u, np.float64, (3 * V,))
+    return cp, keep
+
+
+# -- the C-ABI entry points under their own names --------------------------
+def lbmd_workspace_size(params: lbmd_params) -> int:
+    n = C.c_size_t()
+    _check(load().lbmd_workspace_size(C.byref(params), C.byref(n)), "lbmd_workspace_size")
+    return n.value
+
+
+def lbmd_create(params: lbmd_params, workspace_ptr: int, nbytes: int, stream_ptr: int):
+    h = C.c_void_p()
+    _check(load().lbmd_create(C.byref(params), C.c_void_p(workspace_ptr), nbytes,
+                              C.c_void_p(stream_ptr), C.byref(h)), "lbmd_create")
+    return h
+
+
+def lbmd_step(ctx, n: int) -> None:
+    _check(load().lbmd_step(ctx, int(n)), "lbmd_step")
+
+
+def lbmd_read_fields(ctx, rho_ptr, u_ptr, dst_is_device: int) -> None:
+    _check(load().lbmd_read_fields(ctx, rho_ptr, u_ptr, dst_is_device), "lbmd_read_fields")
+
+
+def lbmd_read_populations(ctx, f_ptr, dst_is_device: int) -> None:
+    _check(load().lbmd_read_populations(ctx, f_ptr, dst_is_device), "lbmd_read_populations")
+
+
+def lbmd_read_beads(ctx, pos_ptr, vel_ptr, dst_is_device: int) -> None:
+    _check(load().lbmd_read_beads(ctx, pos_ptr, vel_ptr, dst_is_device), "lbmd_read_beads")
+
+
+def lbmd_read_bead_aux(ctx, ui_ptr, j_ptr, dst_is_device: int) -> None:
+    _check(load().lbmd_read_bead_aux(ctx, ui_ptr, j_ptr, dst_is_device), "lbmd_read_bead_aux")
+
+
+def lbmd_status(ctx) -> dict:
+    s, nt, st, tt = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int64()
+    _check(load().lbmd_status(ctx, C.byref(s), C.byref(nt), C.byref(st), C.byref(tt)), "lbmd_status")
+    return dict(step=s.value, n_trans=nt.value, state=st.value, t_transloc=tt.value)
+
+
+def lbmd_set_kernel_timing(ctx, enable: bool) -> None:
+    _check(load().lbmd_set_kernel_timing(ctx, int(bool(enable))), "lbmd_set_kernel_timing")
+
+
+def lbmd_lb_kernel_time(ctx):
+    ms, n = C.c_double(), C.c_int64()
+    _check(load().lbmd_lb_kernel_time(ctx, C.byref(ms), C.byref(n)), "lbmd_lb_kernel_time")
+    return ms.value, n.value
+
+
+def lbmd_destroy(ctx) -> None:
+    _check(load().lbmd_destroy(ctx), "lbmd_destroy")
+
+
+def lbmd_version() -> int:
+    return load().lbmd_version()
+
+
+# -- convenience wrapper owning a torch workspace ---------------------------
+class Simulation:
+    """One box with (optionally) one chain, stepped on the GPU.
+
+    The device workspace is a torch uint8 tensor owned by this object; the
+    stream is the given torch stream (default: the current stream)."""
+
+    def __init__(self, params: dict, init_pos=None, init_vel=None, init_rho=None, init_u=None,
+                 bonds=None, device: str = "cuda", stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.p = full_params(params)
+        self.device = torch.device(device)
+        self.N = int(self.p["n_beads"])
+        self.shape = (int(self.p["nz"]), int(self.p["ny"]), int(self.p["nx"]))
+        self.V = self.shape[0] * self.shape[1] * self.shape[2]
+        cp, keep = make_params(self.p, init_pos, init_vel, init_rho, init_u, bonds)
+        nbytes = lbmd_workspace_size(cp)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            self.ctx = lbmd_create(cp, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        del keep
+        self.workspace_bytes = nbytes
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            lbmd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1) -> None:
+        lbmd_step(self.ctx, n)
+
+    def populations(self) -> np.ndarray:
+        f = np.empty((19,) + self.shape, dtype=np.float32)
+        lbmd_read_populations(self.ctx, f.ctypes.data, 0)
+        return f
+
+    def populations_device(self):
+        import torch
+        f = torch.empty((19,) + self.shape, dtype=torch.float32, device=self.device)
+        lbmd_read_populations(self.ctx, f.data_ptr(), 1)
+        return f
+
+    def fields(self):
+        rho = np.empty(self.shape, dtype=np.float32)
+        u = np.empty((3,) + self.shape, dtype=np.float32)
+        lbmd_read_fields(self.ctx, rho.ctypes.data, u.ctypes.data, 0)
+        return rho, u
+
+    def fields_device(self):
+        import torch
+        rho = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        u = torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device)
+        lbmd_read_fields(self.ctx, rho.data_ptr(), u.data_ptr(), 1)
+        return rho, u
+
+    def beads(self):
+        pos = np.empty((self.N, 3))
+        vel = np.empty((self.N, 3))
+        if self.N:
+            lbmd_read_beads(self.ctx, pos.ctypes.data, vel.ctypes.data, 0)
+        return pos, vel
+
+    def bead_aux(self):
+        ui = np.empty((self.N, 3))
+        J = np.empty((self.N, 3))
+        if self.N:
+            lbmd_read_bead_aux(self.ctx, ui.ctypes.data, J.ctypes.data, 0)
+        return ui, J
+
+    def status(self) -> dict:
+        return lbmd_status(self.ctx)
+
+    def set_kernel_timing(self, enable: bool) -> None:
+        lbmd_set_kernel_timing(self.ctx, enable)
+
+    def lb_kernel_time(self):
+        return lbmd_lb_kernel_time(self.ctx)

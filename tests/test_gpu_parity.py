@@ -1,0 +1,303 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (FP32 path, from the acceptance bar of the method): populations
+within 1e-5 relative element by element after one step and 1e-4 after 1000
+steps; bead positions within 1e-4 (lattice units) over 100 steps.  FP16 / BF16
+deviation storage: bounds derived from the storage precision (see each test).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+GPU_ONLY = ("storage", "init_tg_amp")
+
+
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_0710_1272_gb300 as lb
+    return lb
+
+
+def pair(p, init_pos=None, init_vel=None, init_rho=None, init_u=None, bonds=None, **gpu_kw):
+    lb = _gpu()
+    gp = dict(p)
+    gp.update(gpu_kw)
+    sim = lb.Simulation(gp, init_pos=init_pos, init_vel=init_vel, init_rho=init_rho,
+                        init_u=init_u, bonds=bonds)
+    op = {k: v for k, v in p.items() if k not in GPU_ONLY}
+    orc = oracle.OracleSim(op, init_pos=init_pos, init_vel=init_vel, init_rho=init_rho,
+                           init_u=init_u, bonds=bonds)
+    return sim, orc
+
+
+def rel_err(fg, fo):
+    m = fo != 0
+    assert np.all(fg[~m] == 0)
+    return float(np.max(np.abs(fg[m].astype(np.float64) - fo[m]) / np.abs(fo[m])))
+
+
+LB_CASES = [
+    dict(nx=4, ny=4, nz=4, wall_x=-1, tau=0.8, body_force=(1e-4, 0, 0)),
+    dict(nx=5, ny=4, nz=3, wall_x=2, pore_d=1, pore_y0=1, pore_z0=1, tau=0.6),
+    dict(nx=33, ny=17, nz=5, wall_x=20, pore_d=3, y_walls=1, tau=1.0, forcing="guo",
+         body_force=(1e-5, 2e-6, 0)),
+    dict(nx=32, ny=16, nz=16, wall_x=16, pore_d=3, tau=1.0, body_force=(1e-6, 0, 0)),
+    dict(nx=70, ny=9, nz=4, wall_x=0, wall_thickness=2, pore_d=2, tau=0.7),
+]
+
+
+@pytest.mark.parametrize("case", range(len(LB_CASES)))
+def test_initial_populations(case):
+    p = LB_CASES[case]
+    shape = (p["nz"], p["ny"], p["nx"])
+    rho, u = si.random_flow(shape, seed=case, u_max=0.04)
+    sim, orc = pair(p, init_rho=rho, init_u=u)
+    assert rel_err(sim.populations(), orc.populations()) < 2e-6
+    rg, ug = sim.fields()
+    ro, uo = orc.fields()
+    np.testing.assert_allclose(rg, ro, atol=2e-6)
+    np.testing.assert_allclose(ug, uo, atol=2e-6)
+
+
+@pytest.mark.parametrize("case", range(len(LB_CASES)))
+def test_stream_collide_steps(case):
+    p = LB_CASES[case]
+    shape = (p["nz"], p["ny"], p["nx"])
+    rho, u = si.random_flow(shape, seed=10 + case, u_max=0.04)
+    sim, orc = pair(p, init_rho=rho, init_u=u)
+    sim.step(1)
+    orc.step(1)
+    assert rel_err(sim.populations(), orc.populations()) < 1e-5
+    sim.step(9)
+    orc.step(9)
+    assert rel_err(sim.populations(), orc.populations()) < 2e-5
+    assert sim.status()["step"] == 10
+
+
+@pytest.mark.parametrize("forcing", ["paper", "guo"])
+def test_stream_collide_1000_steps(forcing):
+    p = dict(LB_CASES[3], forcing=forcing)
+    rho, u = si.random_flow((16, 16, 32), seed=3, u_max=0.03)
+    sim, orc = pair(p, init_rho=rho, init_u=u)
+    sim.step(1000)
+    orc.step(1000)
+    assert rel_err(sim.populations(), orc.populations()) < 1e-4
+
+
+def test_storage_precision_variants():
+    """FP16 / BF16 deviation storage: h = f - w rho0 of size |h| <= ~0.01 is
+    kept with 11 (fp16) or 8 (bf16) significant bits, i.e. an absolute error
+    <= 2^-11 * 0.01 (fp16) or 2^-8 * 0.01 (bf16) per rounding; relative to the
+    smallest population (1/36) that is <= 2e-4 and 1.2e-3 per step, and the
+    BGK relaxation keeps it from growing over the 10 steps checked."""
+    p = LB_CASES[3]
+    rho, u = si.random_flow((16, 16, 32), seed=5, u_max=0.03)
+    for storage, tol in (("f16", 6e-4), ("bf16", 4e-3)):
+        sim, orc = pair(p, init_rho=rho, init_u=u, storage=storage)
+        sim.step(10)
+        orc.step(10)
+        err = rel_err(sim.populations(), orc.populations())
+        assert err < tol, (storage, err)
+
+
+def test_taylor_green_decay_on_gpu():
+    """Property at any size: the decay rate of a Taylor-Green vortex follows
+    nu = (tau - 1/2)/3 (Sec. II), on the device-generated initial field."""
+    lb = _gpu()
+    L, A, tau = 64, 0.01, 0.8
+    sim = lb.Simulation(dict(nx=L, ny=L, nz=2, wall_x=-1, tau=tau, init_tg_amp=A))
+    k = 2 * np.pi / L
+    basis = np.sin(k * np.arange(L))[None, :] * np.cos(k * np.arange(L))[:, None]
+    ts, amps = [], []
+    for n in range(0, 2001, 100):
+        if n:
+            sim.step(100)
+        if n >= 500:
+            ux = sim.fields()[1][0, 0].astype(np.float64)
+            ts.append(n)
+            amps.append((ux * basis).sum() / (basis * basis).sum())
+    rate = -np.polyfit(ts, np.log(amps), 1)[0]
+    nu = (tau - 0.5) / 3
+    assert abs(rate / (2 * nu * k * k) - 1) < 2e-3
+
+
+def test_mass_conservation_with_walls():
+    lb = _gpu()
+    p = dict(LB_CASES[3], body_force=(0, 0, 0))
+    rho, u = si.random_flow((16, 16, 32), seed=7, u_max=0.03)
+    sim = lb.Simulation(p, init_rho=rho, init_u=u)
+    m0 = sim.fields()[0].astype(np.float64).sum()
+    sim.step(500)
+    m1 = sim.fields()[0].astype(np.float64).sum()
+    assert abs(m1 / m0 - 1) < 1e-6
+
+
+def test_device_and_host_readouts_agree():
+    lb = _gpu()
+    rho, u = si.random_flow((5, 17, 33), seed=8, u_max=0.03)
+    sim = lb.Simulation(LB_CASES[2], init_rho=rho, init_u=u)
+    sim.step(3)
+    np.testing.assert_array_equal(sim.populations(), sim.populations_device().cpu().numpy())
+    r1, u1 = sim.fields()
+    r2, u2 = sim.fields_device()
+    np.testing.assert_array_equal(r1, r2.cpu().numpy())
+    np.testing.assert_array_equal(u1, u2.cpu().numpy())
+
+
+# -- coupled LB + MD ------------------------------------------------------------
+
+def small_case(seed=0, **kw):
+    p = si.small_translocation(seed)
+    p.update(kw)
+    return p, si.saw_chain(p, seed)
+
+
+def test_coupled_one_step():
+    p, pos = small_case(0)
+    sim, orc = pair(p, init_pos=pos)
+    sim.step(1)
+    orc.step(1)
+    assert rel_err(sim.populations(), orc.populations()) < 1e-5
+    rg, vg = sim.beads()
+    ro, vo = orc.beads()
+    np.testing.assert_allclose(rg, ro, atol=1e-5)
+    np.testing.assert_allclose(vg, vo, atol=1e-5)
+    ug, Jg = sim.bead_aux()
+    uo, Jo = orc.bead_aux()
+    np.testing.assert_allclose(ug, uo, atol=1e-7)
+    np.testing.assert_allclose(Jg, Jo, atol=1e-6)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_coupled_bead_trajectory_100_steps(seed):
+    p, pos = small_case(seed)
+    sim, orc = pair(p, init_pos=pos)
+    for _ in range(10):
+        sim.step(10)
+        orc.step(10)
+        rg = sim.beads()[0]
+        ro = orc.beads()[0]
+        assert np.abs(rg - ro).max() < 1e-4
+    st_g, st_o = sim.status(), orc.status()
+    assert st_g["n_trans"] == st_o["n_trans"] and st_g["state"] == st_o["state"]
+
+
+def test_coupled_populations_1000_steps():
+    p, pos = small_case(0)
+    sim, orc = pair(p, init_pos=pos)
+    sim.step(1000)
+    orc.step(1000)
+    assert rel_err(sim.populations(), orc.populations()) < 1e-4
+
+
+@pytest.mark.parametrize("variant", [
+    dict(coupling="ngp"),
+    dict(kappa_phi=0.05),
+    dict(forcing="guo", body_force=(1e-5, 0, 0)),
+    dict(tau=0.8, gamma=0.3, kT=1e-3),
+])
+def test_coupled_variants_10_steps(variant):
+    p, pos = small_case(2, **variant)
+    sim, orc = pair(p, init_pos=pos)
+    sim.step(10)
+    orc.step(10)
+    assert rel_err(sim.populations(), orc.populations()) < 2e-5
+    assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < 2e-5
+
+
+def test_free_beads_and_single_bead():
+    lb = _gpu()
+    p = dict(si.small_translocation(0, n_beads=5), lj_eps=0.5, kT=1e-3)
+    pos = np.array([[20.0 + 2.5 * i, 3.3 + i, 8.1] for i in range(5)])
+    nb = (np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    sim, orc = pair(p, init_pos=pos, bonds=nb)
+    sim.step(5)
+    orc.step(5)
+    assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < 1e-5
+    p1 = dict(si.small_translocation(0, n_beads=1))
+    sim, orc = pair(p1, init_pos=np.array([[18.3, 7.2, 6.9]]))
+    sim.step(5)
+    orc.step(5)
+    assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < 1e-5
+    assert rel_err(sim.populations(), orc.populations()) < 1e-5
+    del lb
+
+
+def test_coupled_momentum_conservation_on_gpu():
+    """Periodic box, no wall: fluid + bead momentum is conserved by the
+    coupling (property that holds at any size)."""
+    lb = _gpu()
+    p = dict(si.small_translocation(0, n_beads=30))
+    p.update(nx=48, ny=32, nz=32, wall_x=-1, pore_d=0, kT=1e-3, gamma=0.3)
+    pos = si.saw_chain(dict(p), 3)
+    vel = np.random.default_rng(4).normal(0, 0.02, pos.shape)
+    sim = lb.Simulation(p, init_pos=pos, init_vel=vel)
+    c = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+                  [1, 1, 0], [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1], [-1, 0, -1],
+                  [1, 0, -1], [-1, 0, 1], [0, 1, 1], [0, -1, -1], [0, 1, -1], [0, -1, 1]], float)
+
+    def total():
+        f = sim.populations().astype(np.float64)
+        return np.einsum("pzyx,pa->a", f, c) + sim.beads()[1].sum(0)
+
+    P0 = total()
+    for _ in range(5):
+        sim.step(20)
+        assert np.abs(total() - P0).max() < 2e-5
+
+
+def test_translocation_status():
+    p = dict(si.small_translocation(0, n_beads=2), lj_eps=0.0, f_drive=0.0, gamma=0.0, kT=0.0)
+    pos = np.array([[14.0, 7.0, 7.0], [12.8, 7.0, 7.0]])
+    sim, orc = pair(p, init_pos=pos)
+    sim.step(1)
+    orc.step(1)
+    assert sim.status() == orc.status()
+    assert sim.status()["state"] == oracle.TRANSLOCATED and sim.status()["t_transloc"] == 1
+
+
+def test_graph_and_direct_launch_agree():
+    p, pos = small_case(3)
+    lb = _gpu()
+    a = lb.Simulation(p, init_pos=pos)
+    b = lb.Simulation(p, init_pos=pos)
+    b.set_kernel_timing(True)
+    a.step(37)
+    b.step(37)
+    ms, n = b.lb_kernel_time()
+    assert n == 37 and ms > 0
+    np.testing.assert_allclose(a.populations(), b.populations(), rtol=1e-6, atol=1e-9)
+    np.testing.assert_allclose(a.beads()[0], b.beads()[0], atol=1e-6)
+    assert a.status() == b.status()
+
+
+def test_max_chain_length():
+    lb = _gpu()
+    p = dict(si.paper_translocation(0, n_beads=1024))
+    p.update(nx=128, ny=64, nz=64, wall_x=32)
+    pos = si.saw_chain(p, 0)
+    sim, orc = pair(p, init_pos=pos)
+    sim.step(2)
+    orc.step(2)
+    assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < 2e-5
+    del lb
+
+
+def test_paper_sized_box_first_steps():
+    """256 x 128 x 128 box, wall at x = 128 with a 5x5 pore, 400 beads: the
+    full population field and every bead after two steps, in the launch
+    configuration the benchmark times (graph replay)."""
+    p = si.paper_translocation(0)
+    pos = si.saw_chain(p, 0)
+    sim, orc = pair(p, init_pos=pos)
+    sim.step(2)
+    orc.step(2)
+    assert rel_err(sim.populations(), orc.populations()) < 1e-5
+    assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < 1e-5
