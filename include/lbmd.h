@@ -179,6 +179,14 @@ int lbmd_status(lbmd_ctx *ctx, int64_t *step, int32_t *n_trans, int32_t *state,
                 int64_t *t_transloc);
 
 /*
+ * Constraint-solver counters: Newton iterations (summed over the M substeps)
+ * of the last LB step, and the number of LB steps in which a SHAKE solve hit
+ * the iteration cap with a residual above 1e-3 (Sec. II, SHAKE/RATTLE).
+ * Synchronises the stream.  Either pointer may be NULL.
+ */
+int lbmd_solver_stats(lbmd_ctx *ctx, int32_t *newton_iters_last_step, int32_t *failed_steps);
+
+/*
  * Kernel timing for benchmarks: while enabled, lbmd_step launches kernels
  * directly (no graph) and brackets every stream-collide launch with CUDA
  * events on its stream.  lbmd_lb_kernel_time synchronises and returns the

@@ -36,7 +36,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 size_t store_bytes(int storage) { return storage == LBMD_STORE_F32 ? 4 : 2; }
 
 struct Layout {
-  size_t popA, popB, solid, tile, xslab, pos, vel, ui, J, sp_node, sp_w, b0, status, stage;
+  size_t popA, popB, solid, tile, xslab, pos, pos_lo, vel, ui, J, sp_node, sp_w, b0, status, stage;
   size_t stage_floats;  // staging capacity in floats
   size_t total;
   long long Vp;
@@ -68,6 +68,7 @@ Layout make_layout(const lbmd_params &p) {
   L.tile = take(rows * L.ntx);
   L.xslab = take((size_t)p.nx);
   L.pos = take(Np * sizeof(float4));
+  L.pos_lo = take(Np * sizeof(float4));
   L.vel = take(Np * sizeof(float4));
   L.ui = take(Np * sizeof(float4));
   L.J = take(Np * sizeof(float4));
@@ -476,6 +477,7 @@ int lbmd_create(const lbmd_params *params, void *dev_workspace, size_t bytes, vo
   a.shake_tol = (float)p.shake_tol;
   a.seed = p.seed;
   a.pos = (float4 *)(c->ws + L.pos);
+  a.pos_lo = (float4 *)(c->ws + L.pos_lo);
   a.vel = (float4 *)(c->ws + L.vel);
   a.ui = (float4 *)(c->ws + L.ui);
   a.J = (float4 *)(c->ws + L.J);
@@ -485,15 +487,20 @@ int lbmd_create(const lbmd_params *params, void *dev_workspace, size_t bytes, vo
   a.status = c->status;
   const int N = p.n_beads;
   // host staging kept alive until the stream synchronisation below
-  std::vector<float4> hp(std::max(N, 1)), hv(std::max(N, 1)), hz(std::max(N, 1), make_float4(0, 0, 0, 0));
+  std::vector<float4> hp(std::max(N, 1)), hl(std::max(N, 1)), hv(std::max(N, 1)),
+      hz(std::max(N, 1), make_float4(0, 0, 0, 0));
   std::vector<float> hb(std::max(N - 1, 1), 0.f);
   if (N > 0) {
     a.ox = (int)std::floor(p.init_pos[0]);
     a.oy = (int)std::floor(p.init_pos[1]);
     a.oz = (int)std::floor(p.init_pos[2]);
     for (int i = 0; i < N; ++i) {
-      hp[i] = make_float4((float)(p.init_pos[3 * i] - a.ox), (float)(p.init_pos[3 * i + 1] - a.oy),
-                          (float)(p.init_pos[3 * i + 2] - a.oz), 0.f);
+      // local coordinate split into a float hi part and the float remainder
+      const double lx = p.init_pos[3 * i] - a.ox, ly = p.init_pos[3 * i + 1] - a.oy,
+                   lz = p.init_pos[3 * i + 2] - a.oz;
+      hp[i] = make_float4((float)lx, (float)ly, (float)lz, 0.f);
+      hl[i] = make_float4((float)(lx - (double)hp[i].x), (float)(ly - (double)hp[i].y),
+                          (float)(lz - (double)hp[i].z), 0.f);
       hv[i] = p.init_vel ? make_float4((float)p.init_vel[3 * i], (float)p.init_vel[3 * i + 1],
                                        (float)p.init_vel[3 * i + 2], 0.f)
                          : make_float4(0, 0, 0, 0);
@@ -501,6 +508,7 @@ int lbmd_create(const lbmd_params *params, void *dev_workspace, size_t bytes, vo
     for (int k = 0; k + 1 < N; ++k)
       hb[k] = (float)(p.n_constraints > 0 ? p.bond_len[k] : p.bond_length);
     if ((e = cudaMemcpyAsync(a.pos, hp.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(e, "upload");
+    if ((e = cudaMemcpyAsync(a.pos_lo, hl.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(e, "upload");
     if ((e = cudaMemcpyAsync(a.vel, hv.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(e, "upload");
     if ((e = cudaMemcpyAsync(a.ui, hz.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(e, "upload");
     if ((e = cudaMemcpyAsync(a.J, hz.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(e, "upload");
@@ -609,7 +617,7 @@ static int read_bead_pair(lbmd_ctx *c, double *x, double *y, int dst_is_device, 
   if (aux)
     CK(c, launch_read_bead_aux(a.ui, a.J, N, dx, dy, c->user));
   else
-    CK(c, launch_read_beads(a.pos, a.vel, N, a.ox, a.oy, a.oz, dx, dy, c->user));
+    CK(c, launch_read_beads(a.pos, a.pos_lo, a.vel, N, a.ox, a.oy, a.oz, dx, dy, c->user));
   if (!dst_is_device) {
     if (x) CK(c, cudaMemcpyAsync(x, dx, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->user));
     if (y) CK(c, cudaMemcpyAsync(y, dy, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->user));
@@ -636,6 +644,17 @@ int lbmd_status(lbmd_ctx *c, int64_t *step, int32_t *n_trans, int32_t *state, in
   if (n_trans) *n_trans = st.n_trans;
   if (state) *state = st.state;
   if (t_transloc) *t_transloc = st.t_transloc;
+  return LBMD_OK;
+}
+
+int lbmd_solver_stats(lbmd_ctx *c, int32_t *newton_iters_last_step, int32_t *failed_steps) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  DevStatus st;
+  CK(c, cudaMemcpyAsync(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost, c->user));
+  CK(c, cudaStreamSynchronize(c->user));
+  if (newton_iters_last_step) *newton_iters_last_step = st.newton_iters;
+  if (failed_steps) *failed_steps = st.shake_fail;
   return LBMD_OK;
 }
 

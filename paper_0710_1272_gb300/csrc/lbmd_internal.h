@@ -16,7 +16,8 @@ struct DevStatus {
   int n_trans;           // beads with unwrapped x < wall_x
   int max_trans;         // largest N_T seen
   int state;             // LBMD_RUNNING, ...
-  int shake_fail;        // constraint solves that hit the iteration cap
+  int shake_fail;        // LB steps whose constraint solve hit the iteration cap
+  int newton_iters;      // Newton iterations of the last LB step (all substeps)
 };
 
 // Lattice geometry as the kernels see it.
@@ -50,7 +51,8 @@ struct ChainArgs {
   float dt, mass, gamma, kT, sigma, eps, kappa, fdrive, shake_tol;
   unsigned long long seed;
   int ox, oy, oz;           // integer origin of the chain's local frame
-  float4 *pos, *vel;        // local positions (unwrapped - origin), velocities
+  float4 *pos, *pos_lo;     // local positions (unwrapped - origin) as hi + lo
+  float4 *vel;
   float4 *ui, *J;           // interpolated u and impulse of the last step
   int *sp_node;             // [8N] grid node of each transfer weight, -1 none
   float *sp_w;              // [8N] renormalised transfer weights
@@ -59,6 +61,7 @@ struct ChainArgs {
 };
 
 size_t md_smem_bytes(int N);
+int md_threads(int N);
 // Opt the MD kernel into the dynamic shared memory a chain of N beads needs.
 cudaError_t md_prepare(int storage, int N);
 
@@ -79,8 +82,8 @@ cudaError_t launch_md_cycle(int storage, const ChainArgs &a, cudaStream_t s);
 cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, const float *sp_w,
                           const float4 *J, int N, int nw, void *dst, DevStatus *bump,
                           cudaStream_t s);
-cudaError_t launch_read_beads(const float4 *pos, const float4 *vel, int N, int ox, int oy,
-                              int oz, double *dpos, double *dvel, cudaStream_t s);
+cudaError_t launch_read_beads(const float4 *pos, const float4 *pos_lo, const float4 *vel, int N,
+                              int ox, int oy, int oz, double *dpos, double *dvel, cudaStream_t s);
 cudaError_t launch_read_bead_aux(const float4 *ui, const float4 *J, int N, double *dui,
                                  double *dJ, cudaStream_t s);
 

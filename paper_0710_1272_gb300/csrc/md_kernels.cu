@@ -32,16 +32,41 @@ __device__ __forceinline__ F3 operator-(F3 a, F3 b) { return F3{a.x - b.x, a.y -
 __device__ __forceinline__ F3 operator*(float s, F3 a) { return F3{s * a.x, s * a.y, s * a.z}; }
 __device__ __forceinline__ float dot(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
-size_t md_smem_bytes(int N) {
-  // s_r, s_t, s_b, s_v (float4 each), two PCR buffers of (a, b, c, d), x
-  return (size_t)N * (4 * sizeof(float4) + 9 * sizeof(float));
+// Threads of the MD block for a chain of N beads: enough to give every
+// (bead, corner) pair of the gather its own thread and to split the pair-force
+// loop, at most 1024.
+int md_threads(int N) {
+  const int n32 = (N + 31) / 32 * 32;
+  return n32 >= 256 ? 1024 : (4 * n32 < 128 ? 128 : 4 * n32);
 }
 
-// Split an unwrapped local coordinate into a wrapped node index and the
-// fraction in [0, 1): global = origin + local.
-__device__ __forceinline__ void cell_frac(float local, int origin, int n, int &cell, float &frac) {
-  const float fl = floorf(local);
-  frac = local - fl;
+size_t md_smem_bytes(int N) {
+  const int T = md_threads(N);
+  const int n32 = (N + 31) / 32 * 32;
+  const int nsplit = T / n32;
+  // s_rh, s_rl, s_ui, s_t, s_b, s_v (float4), PCR (8 floats), x, partial forces
+  return (size_t)N * (6 * sizeof(float4) + 9 * sizeof(float)) +
+         (size_t)(nsplit - 1) * n32 * sizeof(float4);
+}
+
+// Double-float helpers: a coordinate is hi + lo with |lo| <= ulp(hi) / 2.
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float d) {
+  const float s = hi + d;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (d - bp);
+  const float l = lo + e;
+  hi = s + l;
+  lo = l - (hi - s);
+}
+__device__ __forceinline__ F3 diff_hl(float4 ah, float4 al, float4 bh, float4 bl) {
+  return F3{(ah.x - bh.x) + (al.x - bl.x), (ah.y - bh.y) + (al.y - bl.y),
+            (ah.z - bh.z) + (al.z - bl.z)};
+}
+// Wrapped node index and fraction of global = origin + hi + lo.
+__device__ __forceinline__ void cell_frac_hl(float hi, float lo, int origin, int n, int &cell,
+                                             float &frac) {
+  const float fl = floorf(hi);
+  frac = (hi - fl) + lo;
   cell = wrapi(origin + (int)fl, n);
 }
 
@@ -99,10 +124,10 @@ __device__ __forceinline__ void wca_add(F3 d, float sig2, float rc2, float eps24
   }
 }
 
-// Eq. 3 bending at the angle of beads (a, b, c): returns the force on the
-// bead at position `which` (0 = a, 1 = b, 2 = c).
-__device__ __forceinline__ F3 bend_force(F3 ra, F3 rb, F3 rc, float kappa, int which) {
-  const F3 b1 = rb - ra, b2 = rc - rb;
+// Eq. 3 bending at the angle of beads (a, b, c) given the two bond vectors
+// b1 = r_b - r_a and b2 = r_c - r_b: the force on bead `which` (0 = a, 1 = b,
+// 2 = c), F = -dV/dr with V = kappa phi^2 / 2.
+__device__ __forceinline__ F3 bend_force(F3 b1, F3 b2, float kappa, int which) {
   const float l1 = sqrtf(dot(b1, b1)), l2 = sqrtf(dot(b2, b2));
   float cphi = dot(b1, b2) / (l1 * l2);
   cphi = fminf(1.f, fmaxf(-1.f, cphi));
@@ -115,102 +140,129 @@ __device__ __forceinline__ F3 bend_force(F3 ra, F3 rb, F3 rc, float kappa, int w
   return A * g2;
 }
 
+// Stage (1) for (bead, corner) pair e = 8 i + k handled by one thread; the
+// eight lanes of a bead are consecutive, so the weight normalisation and the
+// sum over corners are lane shuffles.  Writes the transfer weights for the
+// spread and returns the bead's interpolated u on the corner-0 lane.
 template <int S>
-__device__ void gather_bead(const ChainArgs &a, F3 r, int i, F3 &ui) {
+__device__ F3 gather_pair(const ChainArgs &a, int e, bool valid, const float4 *s_rh,
+                          const float4 *s_rl) {
   using T = typename Store<S>::T;
   const LbGeom &g = a.geo;
-  int c0[3];
-  float s[3];
-  cell_frac(r.x, a.ox, g.nx, c0[0], s[0]);
-  cell_frac(r.y, a.oy, g.ny, c0[1], s[1]);
-  cell_frac(r.z, a.oz, g.nz, c0[2], s[2]);
-  int node[8];
-  float w[8];
-  float wsum = 0.f;
-  if (a.coupling == LBMD_COUPLING_NGP) {
-    const int x = s[0] >= 0.5f ? wrap_p1(c0[0], g.nx) : c0[0];
-    const int y = s[1] >= 0.5f ? wrap_p1(c0[1], g.ny) : c0[1];
-    const int z = s[2] >= 0.5f ? wrap_p1(c0[2], g.nz) : c0[2];
-    const bool sol = solid_at(g.solid, g.ntx, g.ny, x, y, z);
-    node[0] = sol ? -1 : (int)(((size_t)z * g.ny + y) * g.nx + x);
-    w[0] = sol ? 0.f : 1.f;
-    wsum = w[0];
-#pragma unroll
-    for (int k = 1; k < 8; ++k) {
-      node[k] = -1;
-      w[k] = 0.f;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
+  const int i = e >> 3, k = e & 7;
+  int node = -1;
+  float w = 0.f;
+  if (valid) {
+    const float4 rh = s_rh[i], rl = s_rl[i];
+    int c0[3];
+    float s[3];
+    cell_frac_hl(rh.x, rl.x, a.ox, g.nx, c0[0], s[0]);
+    cell_frac_hl(rh.y, rl.y, a.oy, g.ny, c0[1], s[1]);
+    cell_frac_hl(rh.z, rl.z, a.oz, g.nz, c0[2], s[2]);
+    int x, y, z;
+    if (a.coupling == LBMD_COUPLING_NGP) {
+      x = s[0] >= 0.5f ? wrap_p1(c0[0], g.nx) : c0[0];
+      y = s[1] >= 0.5f ? wrap_p1(c0[1], g.ny) : c0[1];
+      z = s[2] >= 0.5f ? wrap_p1(c0[2], g.nz) : c0[2];
+      w = k == 0 ? 1.f : 0.f;
+    } else {
       const int ox = k & 1, oy = (k >> 1) & 1, oz = (k >> 2) & 1;
-      const int x = ox ? wrap_p1(c0[0], g.nx) : c0[0];
-      const int y = oy ? wrap_p1(c0[1], g.ny) : c0[1];
-      const int z = oz ? wrap_p1(c0[2], g.nz) : c0[2];
-      const bool sol = solid_at(g.solid, g.ntx, g.ny, x, y, z);
-      const float wk = (ox ? s[0] : 1.f - s[0]) * (oy ? s[1] : 1.f - s[1]) * (oz ? s[2] : 1.f - s[2]);
-      node[k] = sol ? -1 : (int)(((size_t)z * g.ny + y) * g.nx + x);
-      w[k] = sol ? 0.f : wk;
-      wsum += w[k];
+      x = ox ? wrap_p1(c0[0], g.nx) : c0[0];
+      y = oy ? wrap_p1(c0[1], g.ny) : c0[1];
+      z = oz ? wrap_p1(c0[2], g.nz) : c0[2];
+      w = (ox ? s[0] : 1.f - s[0]) * (oy ? s[1] : 1.f - s[1]) * (oz ? s[2] : 1.f - s[2]);
+    }
+    if (w != 0.f && !solid_at(g.solid, g.ntx, g.ny, x, y, z))
+      node = (int)(((size_t)z * g.ny + y) * g.nx + x);
+    else
+      w = 0.f;
+  }
+  float wsum = w;
+  wsum += __shfl_xor_sync(0xffffffffu, wsum, 1);
+  wsum += __shfl_xor_sync(0xffffffffu, wsum, 2);
+  wsum += __shfl_xor_sync(0xffffffffu, wsum, 4);
+  const float wn = wsum > 0.f ? w / wsum : 0.f;
+  if (wn == 0.f) node = -1;
+  F3 u{0.f, 0.f, 0.f};
+  if (valid) {
+    a.sp_node[e] = node;
+    a.sp_w[e] = wn;
+    if (node >= 0) {
+      const int x = node % g.nx, yz = node / g.nx;
+      float h[kQ];
+      pull19<S, true>(g, (const T *)a.f, x, yz % g.ny, yz / g.ny, h);
+      float drho, jx, jy, jz;
+      moments19(h, drho, jx, jy, jz);
+      if (a.forcing == LBMD_FORCING_GUO) {
+        jx += 0.5f * a.g[0];
+        jy += 0.5f * a.g[1];
+        jz += 0.5f * a.g[2];
+      }
+      const float rinv = wn / (a.rho0 + drho);
+      u = F3{jx * rinv, jy * rinv, jz * rinv};
     }
   }
-  ui = F3{0.f, 0.f, 0.f};
-  const float inv = wsum > 0.f ? 1.0f / wsum : 0.f;
-#pragma unroll 1
-  for (int k = 0; k < 8; ++k) {
-    const float wk = w[k] * inv;
-    a.sp_node[8 * i + k] = node[k];
-    a.sp_w[8 * i + k] = wk;
-    if (node[k] < 0) continue;
-    const int x = node[k] % g.nx, yz = node[k] / g.nx;
-    const int y = yz % g.ny, z = yz / g.ny;
-    float h[kQ];
-    pull19<S, true>(g, (const T *)a.f, x, y, z, h);
-    float drho, jx, jy, jz;
-    moments19(h, drho, jx, jy, jz);
-    if (a.forcing == LBMD_FORCING_GUO) {
-      jx += 0.5f * a.g[0];
-      jy += 0.5f * a.g[1];
-      jz += 0.5f * a.g[2];
-    }
-    const float rinv = wk / (a.rho0 + drho);
-    ui = ui + F3{jx * rinv, jy * rinv, jz * rinv};
+#pragma unroll
+  for (int m = 1; m < 8; m <<= 1) {
+    u.x += __shfl_xor_sync(0xffffffffu, u.x, m);
+    u.y += __shfl_xor_sync(0xffffffffu, u.y, m);
+    u.z += __shfl_xor_sync(0xffffffffu, u.z, m);
   }
+  return u;
 }
 
-// Conservative + external forces on bead i (WCA pairs, bending, wall, drive).
-__device__ F3 bead_forces(const ChainArgs &a, int i, F3 r, const float4 *s_r) {
+// WCA pair forces on bead i from beads j in [j0, j1) (non-bonded pairs,
+// minimum image), with separations from the double-float positions.
+__device__ __forceinline__ F3 pair_forces(const ChainArgs &a, int i, int j0, int j1,
+                                          const float4 *s_rh, const float4 *s_rl) {
   const LbGeom &g = a.geo;
-  const int N = a.N;
   const float sig2 = a.sigma * a.sigma;
   const float rc = kTwoSixth * a.sigma, rc2 = rc * rc;
   const float eps24 = 24.0f * a.eps;
   const float Lx = (float)g.nx, Ly = (float)g.ny, Lz = (float)g.nz;
+  const float iLx = 1.0f / Lx, iLy = 1.0f / Ly, iLz = 1.0f / Lz;
+  const float4 rh = s_rh[i], rl = s_rl[i];
   F3 F{0.f, 0.f, 0.f};
-  if (a.eps != 0.f) {
-    for (int j = 0; j < N; ++j) {
-      const int dij = j - i;
-      if (dij == 0 || (a.has_bonds && (dij == 1 || dij == -1))) continue;
-      F3 d = r - f3(s_r[j]);
-      d.x -= Lx * floorf(d.x / Lx + 0.5f);
-      d.y -= Ly * floorf(d.y / Ly + 0.5f);
-      d.z -= Lz * floorf(d.z / Lz + 0.5f);
-      wca_add(d, sig2, rc2, eps24, F);
-    }
+  for (int j = j0; j < j1; ++j) {
+    const int dij = j - i;
+    if (dij == 0 || (a.has_bonds && (dij == 1 || dij == -1))) continue;
+    F3 d = diff_hl(rh, rl, s_rh[j], s_rl[j]);
+    d.x -= Lx * rintf(d.x * iLx);
+    d.y -= Ly * rintf(d.y * iLy);
+    d.z -= Lz * rintf(d.z * iLz);
+    wca_add(d, sig2, rc2, eps24, F);
   }
+  return F;
+}
+
+// Bending, wall and drive forces on bead i.
+__device__ F3 local_forces(const ChainArgs &a, int i, const float4 *s_rh, const float4 *s_rl) {
+  const LbGeom &g = a.geo;
+  const int N = a.N;
+  F3 F{0.f, 0.f, 0.f};
   if (a.kappa != 0.f && a.has_bonds) {
-    if (i >= 2) F = F + bend_force(f3(s_r[i - 2]), f3(s_r[i - 1]), r, a.kappa, 2);
-    if (i >= 1 && i + 1 < N) F = F + bend_force(f3(s_r[i - 1]), r, f3(s_r[i + 1]), a.kappa, 1);
-    if (i + 2 < N) F = F + bend_force(r, f3(s_r[i + 1]), f3(s_r[i + 2]), a.kappa, 0);
+    // bond vectors b_{i-2}, b_{i-1}, b_i, b_{i+1} around bead i
+    F3 bm2{0, 0, 0}, bm1{0, 0, 0}, b0{0, 0, 0}, bp1{0, 0, 0};
+    if (i >= 2) bm2 = diff_hl(s_rh[i - 1], s_rl[i - 1], s_rh[i - 2], s_rl[i - 2]);
+    if (i >= 1) bm1 = diff_hl(s_rh[i], s_rl[i], s_rh[i - 1], s_rl[i - 1]);
+    if (i + 1 < N) b0 = diff_hl(s_rh[i + 1], s_rl[i + 1], s_rh[i], s_rl[i]);
+    if (i + 2 < N) bp1 = diff_hl(s_rh[i + 2], s_rl[i + 2], s_rh[i + 1], s_rl[i + 1]);
+    if (i >= 2) F = F + bend_force(bm2, bm1, a.kappa, 2);
+    if (i >= 1 && i + 1 < N) F = F + bend_force(bm1, b0, a.kappa, 1);
+    if (i + 2 < N) F = F + bend_force(b0, bp1, a.kappa, 0);
   }
-  // wall: Eq. 2 between the bead and every solid node within the cutoff
+  const float4 rh = s_rh[i], rl = s_rl[i];
   int c[3];
   float s[3];
-  cell_frac(r.x, a.ox, g.nx, c[0], s[0]);
-  cell_frac(r.y, a.oy, g.ny, c[1], s[1]);
-  cell_frac(r.z, a.oz, g.nz, c[2], s[2]);
+  cell_frac_hl(rh.x, rl.x, a.ox, g.nx, c[0], s[0]);
+  cell_frac_hl(rh.y, rl.y, a.oy, g.ny, c[1], s[1]);
+  cell_frac_hl(rh.z, rl.z, a.oz, g.nz, c[2], s[2]);
   if (a.eps != 0.f) {
-    // node offsets n with |n - s| < rc along each axis: n in [ceil(s - rc), floor(s + rc)]
+    // wall: Eq. 2 between the bead and every solid node closer than the cutoff;
+    // node offsets n with |n - s| < rc: n in [ceil(s - rc), floor(s + rc)]
+    const float sig2 = a.sigma * a.sigma;
+    const float rc = kTwoSixth * a.sigma, rc2 = rc * rc;
+    const float eps24 = 24.0f * a.eps;
     const int lo0 = (int)ceilf(s[0] - rc), hi0 = (int)floorf(s[0] + rc);
     const int lo1 = (int)ceilf(s[1] - rc), hi1 = (int)floorf(s[1] + rc);
     const int lo2 = (int)ceilf(s[2] - rc), hi2 = (int)floorf(s[2] + rc);
@@ -231,7 +283,7 @@ __device__ F3 bead_forces(const ChainArgs &a, int i, F3 r, const float4 *s_r) {
   }
   // pulling force of Sec. III inside the channel through the pore
   if (a.has_wall && a.pore_d > 0 && a.fdrive != 0.f) {
-    int di = wrapi(c[0] - a.wall_x + g.nx / 2, g.nx) - g.nx / 2;
+    const int di = wrapi(c[0] - a.wall_x + g.nx / 2, g.nx) - g.nx / 2;
     const float dx = (float)di + s[0] - 0.5f * (float)(a.wall_t - 1);
     const float half = 0.5f * (float)(a.wall_t - 1) + 1.5f;
     const float ry = (float)c[1] + s[1], rz = (float)c[2] + s[2];
@@ -246,58 +298,86 @@ template <int S>
 __global__ void __launch_bounds__(1024) k_md_cycle(ChainArgs a) {
   extern __shared__ float4 smem4[];
   const int N = a.N;
-  const int i = threadIdx.x;
+  const int T = blockDim.x;
+  const int t = threadIdx.x;
+  const int i = t;  // bead of this thread in the per-bead phases
   const bool bead = i < N;
-  float4 *s_r = smem4;       // positions at the start of the substep
-  float4 *s_t = s_r + N;     // trial / constrained positions
+  const int n32 = (N + 31) / 32 * 32;
+  const int nsplit = T / n32;
+  float4 *s_rh = smem4;      // positions, hi part (start of the substep)
+  float4 *s_rl = s_rh + N;   // positions, lo part
+  float4 *s_ui = s_rl + N;   // interpolated fluid velocity
+  float4 *s_t = s_ui + N;    // displacement of the substep
   float4 *s_b = s_t + N;     // bond vectors
   float4 *s_v = s_b + N;     // velocities (RATTLE)
-  float *tri = (float *)(s_v + N);  // 8N: two PCR buffers
-  float *s_x = tri + 8 * N;         // N: PCR solution
+  float4 *s_fp = s_v + N;    // partial pair forces of splits 1..nsplit-1
+  float *tri = (float *)(s_fp + (nsplit - 1) * n32);  // 8N: two PCR buffers
+  float *s_x = tri + 8 * N;                             // N: PCR solution
 
   const long long step = a.status->step;
-  F3 r{0.f, 0.f, 0.f}, v{0.f, 0.f, 0.f}, ui{0.f, 0.f, 0.f}, J{0.f, 0.f, 0.f};
+  float4 rh = make_float4(0, 0, 0, 0), rl = rh;
+  F3 v{0.f, 0.f, 0.f};
   if (bead) {
-    r = f3(a.pos[i]);
+    rh = a.pos[i];
+    rl = a.pos_lo[i];
     v = f3(a.vel[i]);
-    // (1) interpolation of the fluid velocity, frozen for the M substeps
-    gather_bead<S>(a, r, i, ui);
+    s_rh[i] = rh;
+    s_rl[i] = rl;
   }
-  const float dt = a.dt, m = a.mass, im = 1.0f / a.mass;
+  __syncthreads();
+  // (1) interpolation of the fluid velocity, frozen for the M substeps
+  for (int e0 = 0; e0 < 8 * N; e0 += T) {
+    const int e = e0 + t;
+    const F3 u = gather_pair<S>(a, e, e < 8 * N, s_rh, s_rl);
+    if (e < 8 * N && (e & 7) == 0) s_ui[e >> 3] = f4(u);
+  }
+  __syncthreads();
+  const F3 ui = bead ? f3(s_ui[i]) : F3{0.f, 0.f, 0.f};
+  F3 J{0.f, 0.f, 0.f};
+  const float dt = a.dt, m = a.mass, im = 1.0f / a.mass, idt = 1.0f / a.dt;
   const float sig_r = sqrtf(2.0f * m * a.gamma * a.kT / dt);
   const float b0 = (bead && i < N - 1 && a.has_bonds) ? a.b0[i] : 1.f;
-  const float tol = fmaxf(a.shake_tol, 2e-5f);
-  int shake_bad = 0;
+  const float tol = fmaxf(a.shake_tol, 1e-6f);
+  int shake_bad = 0, newton_total = 0;
+  const int fsplit = t / n32, fi = t - fsplit * n32;  // pair-force split of this thread
+  const int chunk = (N + nsplit - 1) / nsplit;
 
   for (int k = 0; k < a.M; ++k) {  // (2) M MD substeps
-    if (bead) s_r[i] = f4(r);
+    // pair forces, the j-range split over nsplit groups of threads
+    F3 Fp{0.f, 0.f, 0.f};
+    if (a.eps != 0.f && fi < N && fsplit < nsplit)
+      Fp = pair_forces(a, fi, fsplit * chunk, min(N, (fsplit + 1) * chunk), s_rh, s_rl);
+    if (fsplit >= 1 && fsplit < nsplit && fi < N) s_fp[(fsplit - 1) * n32 + fi] = f4(Fp);
     __syncthreads();
-    F3 rt{0.f, 0.f, 0.f};
+    F3 D{0.f, 0.f, 0.f};
     if (bead) {
-      const F3 Fc = bead_forces(a, i, r, s_r);
+      F3 Fc = Fp;
+      for (int q = 1; q < nsplit; ++q) Fc = Fc + f3(s_fp[(q - 1) * n32 + i]);
+      Fc = Fc + local_forces(a, i, s_rh, s_rl);
       const float3 xi = gauss3(a.seed, (uint32_t)i, step, (uint32_t)k, 0u);
       const F3 fdrag = (-m * a.gamma) * (v - ui);
       const F3 fr = sig_r * F3{xi.x, xi.y, xi.z};
       v = v + (dt * im) * (Fc + fdrag + fr);
       J = J + dt * (fdrag + fr);
-      rt = r + dt * v;
+      D = dt * v;  // unconstrained displacement r~ - r
     }
     if (a.has_bonds) {
-      // SHAKE: r'_i = r~_i + (lam_i s_i - lam_{i-1} s_{i-1}) / m with the old
-      // bond vectors s_b; Newton on G_b = |d_b|^2 - b0^2 = 0.
+      // SHAKE on displacements: D_i = dt v_i + (lam_i s_i - lam_{i-1} s_{i-1}) / m
+      // with the old bond vectors s_b; Newton on G_b = |s_b + D_{b+1} - D_b|^2 - b0^2.
       if (bead) {
-        s_t[i] = f4(rt);
-        if (i < N - 1) s_b[i] = f4(f3(s_r[i + 1]) - r);
+        s_t[i] = f4(D);
+        if (i < N - 1) s_b[i] = f4(diff_hl(s_rh[i + 1], s_rl[i + 1], rh, rl));
       }
       __syncthreads();
       for (int it = 0;; ++it) {
         float G = 0.f, diag = 1.f, sub = 0.f, sup = 0.f;
         bool ok = true;
         if (i < N - 1) {
-          const F3 d = f3(s_t[i + 1]) - f3(s_t[i]);
+          const F3 sb = f3(s_b[i]);
+          const F3 d = sb + (f3(s_t[i + 1]) - f3(s_t[i]));
           G = dot(d, d) - b0 * b0;
           ok = fabsf(G) <= tol * b0 * b0;
-          diag = -4.0f * im * dot(d, f3(s_b[i]));
+          diag = -4.0f * im * dot(d, sb);
           if (i > 0) sub = 2.0f * im * dot(d, f3(s_b[i - 1]));
           if (i < N - 2) sup = 2.0f * im * dot(d, f3(s_b[i + 1]));
         }
@@ -307,41 +387,42 @@ __global__ void __launch_bounds__(1024) k_md_cycle(ChainArgs a) {
           if (__syncthreads_or(bad)) shake_bad = 1;
           break;
         }
+        ++newton_total;
         const float x = pcr_solve(N - 1, sub, diag, sup, -G, tri, N);
         if (i < N - 1) s_x[i] = x;
         __syncthreads();
         if (bead) {
-          F3 t = f3(s_t[i]);
-          if (i < N - 1) t = t + (s_x[i] * im) * f3(s_b[i]);
-          if (i > 0) t = t - (s_x[i - 1] * im) * f3(s_b[i - 1]);
-          s_t[i] = f4(t);
+          F3 dd = f3(s_t[i]);
+          if (i < N - 1) dd = dd + (s_x[i] * im) * f3(s_b[i]);
+          if (i > 0) dd = dd - (s_x[i - 1] * im) * f3(s_b[i - 1]);
+          s_t[i] = f4(dd);
         }
         __syncthreads();
       }
-      if (bead) rt = f3(s_t[i]);
+      if (bead) D = f3(s_t[i]);
     }
     if (bead) {
-      v = (1.0f / dt) * (rt - r);
-      r = rt;
+      // v = (r' - r) / dt evaluated as D / dt (no cancellation); r' = r + D
+      v = idt * D;
+      two_sum_add(rh.x, rl.x, D.x);
+      two_sum_add(rh.y, rl.y, D.y);
+      two_sum_add(rh.z, rl.z, D.z);
     }
     if (a.has_bonds) {
-      // RATTLE: v_i += (mu_i d_i - mu_{i-1} d_{i-1}) / m with d_b the new bonds,
-      // chosen so that d_b . (v_{b+1} - v_b) = 0 for every bond.
-      __syncthreads();  // every read of s_t / s_b above is done
-      if (bead) {
-        s_r[i] = f4(r);
-        s_v[i] = f4(v);
-      }
-      __syncthreads();
-      if (i < N - 1) s_b[i] = f4(f3(s_r[i + 1]) - r);
+      // RATTLE: v_i += (mu_i d_i - mu_{i-1} d_{i-1}) / m with the new bond
+      // vectors d_b = s_b + D_{b+1} - D_b, so that d_b . (v_{b+1} - v_b) = 0.
+      if (bead) s_v[i] = f4(v);
+      F3 dnew{0.f, 0.f, 0.f};
+      if (i < N - 1) dnew = f3(s_b[i]) + (f3(s_t[i + 1]) - f3(s_t[i]));
+      __syncthreads();  // s_v complete; every read of s_b / s_t above done
+      if (i < N - 1) s_b[i] = f4(dnew);
       __syncthreads();
       float rhs = 0.f, diag = 1.f, sub = 0.f, sup = 0.f;
       if (i < N - 1) {
-        const F3 d = f3(s_b[i]);
-        rhs = dot(d, f3(s_v[i + 1]) - v);
-        diag = -2.0f * im * dot(d, d);
-        if (i > 0) sub = im * dot(d, f3(s_b[i - 1]));
-        if (i < N - 2) sup = im * dot(d, f3(s_b[i + 1]));
+        rhs = dot(dnew, f3(s_v[i + 1]) - v);
+        diag = -2.0f * im * dot(dnew, dnew);
+        if (i > 0) sub = im * dot(dnew, f3(s_b[i - 1]));
+        if (i < N - 2) sup = im * dot(dnew, f3(s_b[i + 1]));
       }
       const float mu = pcr_solve(N - 1, sub, diag, sup, -rhs, tri, N);
       if (i < N - 1) s_x[i] = mu;
@@ -351,28 +432,35 @@ __global__ void __launch_bounds__(1024) k_md_cycle(ChainArgs a) {
         if (i > 0) v = v - (s_x[i - 1] * im) * f3(s_b[i - 1]);
       }
     }
-    __syncthreads();  // s_r is rewritten at the top of the next substep
+    __syncthreads();  // every read of s_rh / s_rl of this substep is done
+    if (bead) {
+      s_rh[i] = rh;
+      s_rl[i] = rl;
+    }
+    __syncthreads();
   }
 
   if (bead) {
-    a.pos[i] = f4(r);
+    a.pos[i] = rh;
+    a.pos_lo[i] = rl;
     a.vel[i] = f4(v);
     a.ui[i] = f4(ui);
     a.J[i] = f4(J);
   }
-  // Translocation bookkeeping (Sec. III)
-  const float xrel = bead ? (float)(a.ox - a.wall_x) + r.x : 0.f;
-  const bool finite = isfinite(r.x) && isfinite(r.y) && isfinite(r.z) && isfinite(v.x) &&
+  // Translocation bookkeeping (Sec. III): unwrapped x = origin + hi + lo
+  const float xrel = bead ? ((float)(a.ox - a.wall_x) + rh.x) + rl.x : 0.f;
+  const bool finite = isfinite(rh.x) && isfinite(rh.y) && isfinite(rh.z) && isfinite(v.x) &&
                       isfinite(v.y) && isfinite(v.z);
   const int nt = __syncthreads_count(bead && a.has_wall && xrel < 0.f);
   const int nan = __syncthreads_or(bead && !finite);
   const int out = __syncthreads_and(!bead || xrel > (float)(a.wall_t - 1) + 1.5f);
   const int bad = __syncthreads_or(shake_bad);
-  if (i == 0) {
+  if (t == 0) {
     DevStatus *st = a.status;
     st->n_trans = nt;
     if (nt > st->max_trans) st->max_trans = nt;
     if (bad) st->shake_fail += 1;
+    st->newton_iters = newton_total;
     if (st->state == LBMD_RUNNING) {
       if (nan)
         st->state = LBMD_NAN;
@@ -405,7 +493,7 @@ cudaError_t md_prepare(int storage, int N) {
 
 cudaError_t launch_md_cycle(int storage, const ChainArgs &a, cudaStream_t s) {
   if (a.N <= 0) return cudaSuccess;
-  const int threads = ((a.N + 31) / 32) * 32;
+  const int threads = md_threads(a.N);
   const size_t smem = md_smem_bytes(a.N);
   switch (storage) {
     case LBMD_STORE_F32: k_md_cycle<LBMD_STORE_F32><<<1, threads, smem, s>>>(a); break;
@@ -483,15 +571,16 @@ cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, cons
   return cudaGetLastError();
 }
 
-__global__ void k_read_beads(const float4 *pos, const float4 *vel, int N, int ox, int oy, int oz,
-                             double *dpos, double *dvel) {
+__global__ void k_read_beads(const float4 *pos, const float4 *pos_lo, const float4 *vel, int N,
+                             int ox, int oy, int oz, double *dpos, double *dvel) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   if (dpos) {
     const float4 r = pos[i];
-    dpos[3 * i] = (double)ox + (double)r.x;
-    dpos[3 * i + 1] = (double)oy + (double)r.y;
-    dpos[3 * i + 2] = (double)oz + (double)r.z;
+    const float4 l = pos_lo ? pos_lo[i] : make_float4(0, 0, 0, 0);
+    dpos[3 * i] = (double)ox + (double)r.x + (double)l.x;
+    dpos[3 * i + 1] = (double)oy + (double)r.y + (double)l.y;
+    dpos[3 * i + 2] = (double)oz + (double)r.z + (double)l.z;
   }
   if (dvel) {
     const float4 v = vel[i];
@@ -501,17 +590,17 @@ __global__ void k_read_beads(const float4 *pos, const float4 *vel, int N, int ox
   }
 }
 
-cudaError_t launch_read_beads(const float4 *pos, const float4 *vel, int N, int ox, int oy, int oz,
-                              double *dpos, double *dvel, cudaStream_t s) {
+cudaError_t launch_read_beads(const float4 *pos, const float4 *pos_lo, const float4 *vel, int N,
+                              int ox, int oy, int oz, double *dpos, double *dvel, cudaStream_t s) {
   if (N <= 0) return cudaSuccess;
-  k_read_beads<<<(N + 255) / 256, 256, 0, s>>>(pos, vel, N, ox, oy, oz, dpos, dvel);
+  k_read_beads<<<(N + 255) / 256, 256, 0, s>>>(pos, pos_lo, vel, N, ox, oy, oz, dpos, dvel);
   return cudaGetLastError();
 }
 
 cudaError_t launch_read_bead_aux(const float4 *ui, const float4 *J, int N, double *dui,
                                  double *dJ, cudaStream_t s) {
   if (N <= 0) return cudaSuccess;
-  k_read_beads<<<(N + 255) / 256, 256, 0, s>>>(ui, J, N, 0, 0, 0, dui, dJ);
+  k_read_beads<<<(N + 255) / 256, 256, 0, s>>>(ui, nullptr, J, N, 0, 0, 0, dui, dJ);
   return cudaGetLastError();
 }
 

@@ -32,7 +32,7 @@ DEFAULTS = dict(
     tau=1.0, rho0=1.0, body_force=(0.0, 0.0, 0.0),
     bead_mass=1.0, gamma=0.1, kT=1e-4, lj_sigma=1.8, lj_eps=1.0,
     kappa_phi=0.0, f_drive=0.02, bond_len=1.2,
-    shake_tol=1e-5, shake_max_iter=12, init_tg_amp=0.0, seed=0,
+    shake_tol=1e-6, shake_max_iter=12, init_tg_amp=0.0, seed=0,
 )
 IGNORED_KEYS = {"hydrodynamics", "bonds"}  # oracle-only keys
 
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True):
     L.lbmd_read_bead_aux.argtypes = [P, P, P, C.c_int]
     L.lbmd_status.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                               C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
+    L.lbmd_solver_stats.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.lbmd_set_kernel_timing.argtypes = [P, C.c_int]
     L.lbmd_lb_kernel_time.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.lbmd_destroy.argtypes = [P]
@@ -97,7 +98,8 @@ def load(build_if_missing: bool = True):
     L.lbmd_last_message.restype = C.c_char_p
     for name in ("lbmd_workspace_size", "lbmd_create", "lbmd_step", "lbmd_read_fields",
                  "lbmd_read_populations", "lbmd_read_beads", "lbmd_read_bead_aux", "lbmd_status",
-                 "lbmd_set_kernel_timing", "lbmd_lb_kernel_time", "lbmd_destroy", "lbmd_version"):
+                 "lbmd_set_kernel_timing", "lbmd_lb_kernel_time", "lbmd_destroy", "lbmd_version",
+                 "lbmd_solver_stats"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -203,6 +205,12 @@ def lbmd_status(ctx) -> dict:
     return dict(step=s.value, n_trans=nt.value, state=st.value, t_transloc=tt.value)
 
 
+def lbmd_solver_stats(ctx):
+    it, bad = C.c_int32(), C.c_int32()
+    _check(load().lbmd_solver_stats(ctx, C.byref(it), C.byref(bad)), "lbmd_solver_stats")
+    return dict(newton_iters_last_step=it.value, failed_steps=bad.value)
+
+
 def lbmd_set_kernel_timing(ctx, enable: bool) -> None:
     _check(load().lbmd_set_kernel_timing(ctx, int(bool(enable))), "lbmd_set_kernel_timing")
 
@@ -302,6 +310,9 @@ class Simulation:
 
     def status(self) -> dict:
         return lbmd_status(self.ctx)
+
+    def solver_stats(self) -> dict:
+        return lbmd_solver_stats(self.ctx)
 
     def set_kernel_timing(self, enable: bool) -> None:
         lbmd_set_kernel_timing(self.ctx, enable)
