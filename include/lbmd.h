@@ -195,6 +195,14 @@ int lbmd_solver_stats(lbmd_ctx *ctx, int32_t *newton_iters_last_step, int32_t *f
 int lbmd_set_kernel_timing(lbmd_ctx *ctx, int enable);
 int lbmd_lb_kernel_time(lbmd_ctx *ctx, double *total_ms, int64_t *launches);
 
+/*
+ * Same timing, per kernel of the step: summed ms of the stream-collide (stage
+ * 4), the MD cycle with the gather (stages 1-2) and the spread (stage 3), and
+ * the number of timed steps.  Synchronises.  Any pointer may be NULL.
+ */
+int lbmd_kernel_times(lbmd_ctx *ctx, double *lb_ms, double *md_ms, double *spread_ms,
+                      int64_t *steps);
+
 /* Release the context's host resources (not the caller's workspace). */
 int lbmd_destroy(lbmd_ctx *ctx);
 

@@ -22,18 +22,27 @@ __device__ __forceinline__ void pull19(const LbGeom &g, const typename Store<S>:
   const int zm = wrap_m1(z, nz), zp = wrap_p1(z, nz);
   const size_t self = ((size_t)z * ny + y) * nx + x;
   const size_t Vp = (size_t)g.Vp;
+  // first every solid test (independent loads of the bitfield), then every
+  // population address, so that the 19 population loads are in flight together
+  uint32_t bb = 0;
+  if (CHECK) {
+#pragma unroll
+    for (int p = 1; p < kQ; ++p) {
+      const int sx = cx(p) == 1 ? xm : (cx(p) == -1 ? xp : x);
+      const int sy = cy(p) == 1 ? ym : (cy(p) == -1 ? yp : y);
+      const int sz = cz(p) == 1 ? zm : (cz(p) == -1 ? zp : z);
+      bb |= (uint32_t)solid_at(g.solid, g.ntx, ny, sx, sy, sz) << p;
+    }
+  }
 #pragma unroll
   for (int p = 0; p < kQ; ++p) {
     // source node x - c_p
     const int sx = cx(p) == 1 ? xm : (cx(p) == -1 ? xp : x);
     const int sy = cy(p) == 1 ? ym : (cy(p) == -1 ? yp : y);
     const int sz = cz(p) == 1 ? zm : (cz(p) == -1 ? zp : z);
-    const size_t sidx = ((size_t)sz * ny + sy) * nx + sx;
-    if (CHECK && p != 0 && solid_at(g.solid, g.ntx, ny, sx, sy, sz)) {
-      h[p] = St::load(src + (size_t)opp(p) * Vp + self);
-    } else {
-      h[p] = St::load(src + (size_t)p * Vp + sidx);
-    }
+    const size_t sidx = (size_t)p * Vp + ((size_t)sz * ny + sy) * nx + sx;
+    const size_t bidx = (size_t)opp(p) * Vp + self;
+    h[p] = St::load(src + (((bb >> p) & 1u) ? bidx : sidx));
   }
 }
 

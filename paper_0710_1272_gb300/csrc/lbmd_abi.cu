@@ -36,7 +36,8 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 size_t store_bytes(int storage) { return storage == LBMD_STORE_F32 ? 4 : 2; }
 
 struct Layout {
-  size_t popA, popB, solid, tile, xslab, pos, pos_lo, vel, ui, J, sp_node, sp_w, b0, status, stage;
+  size_t popA, popB, solid, tile, xslab, pos, pos_lo, vel, ui, J, sp_node, sp_w, b0, nl_cnt, wl_cnt,
+      nl_list, wl_list, nl_ref, lam, status, stage;
   size_t stage_floats;  // staging capacity in floats
   size_t total;
   long long Vp;
@@ -74,7 +75,13 @@ Layout make_layout(const lbmd_params &p) {
   L.J = take(Np * sizeof(float4));
   L.sp_node = take(8 * Np * sizeof(int));
   L.sp_w = take(8 * Np * sizeof(float));
-  L.b0 = take(Np * sizeof(float));
+  L.b0 = take(Np * sizeof(double));
+  L.nl_cnt = take(Np * sizeof(int));
+  L.wl_cnt = take(Np * sizeof(int));
+  L.nl_list = take(Np * kMaxPairs * sizeof(short));
+  L.wl_list = take(Np * kMaxWall * sizeof(float4));
+  L.nl_ref = take(Np * sizeof(float4));
+  L.lam = take(Np * sizeof(float));
   L.status = take(sizeof(DevStatus));
   L.stage = take(L.stage_floats * sizeof(float));
   L.total = o;
@@ -220,13 +227,14 @@ struct lbmd_ctx {
   int N, has_bonds;
   cudaStream_t user;        // caller's stream
   cudaStream_t own, side;   // private streams: steps run on own, MD on side
+  int prio_high;            // greatest stream priority of the device
   cudaEvent_t ev_in, ev_out, ev_fork, ev_join;
   cudaGraphExec_t graph[2][3];  // [starting buffer][1, 2, kBlockSteps steps]
   int sticky;
   int timing;
-  std::vector<cudaEvent_t> tev;  // start/stop pairs around timed stream-collides
+  std::vector<cudaEvent_t> tev;  // per timed step: lb, md, spread start/stop pairs
   size_t tev_used;
-  double timed_ms;
+  double timed_ms[3];            // summed durations of stream-collide, MD, spread
   long long timed_count;
   DevStatus *status;
   float *stage;
@@ -256,37 +264,49 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
   const void *A = c->pop[src];
   void *B = c->pop[1 - src];
   cudaError_t e;
-  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaEvent_t t[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   if (c->timing) {
-    if (c->tev_used + 2 > c->tev.size()) {
-      for (int k = 0; k < 512; ++k) {
+    if (c->tev_used + 6 > c->tev.size()) {
+      for (int k = 0; k < 600; ++k) {
         cudaEvent_t ev;
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
         c->tev.push_back(ev);
       }
     }
-    t0 = c->tev[c->tev_used];
-    t1 = c->tev[c->tev_used + 1];
-    c->tev_used += 2;
+    for (int k = 0; k < 6; ++k) t[k] = c->tev[c->tev_used + k];
+    c->tev_used += 6;
   }
   if (c->N > 0) {
-    if ((e = cudaEventRecord(c->ev_fork, c->own)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(c->side, c->ev_fork, 0)) != cudaSuccess) return e;
+    // (1) gather from the pre-step populations, then fork: the MD cycle runs
+    // on the side stream while the stream-collide runs on the main one
     ChainArgs a = c->chain;
     a.f = A;
-    if ((e = launch_md_cycle(c->p.storage, a, c->side)) != cudaSuccess) return e;
+    if (t[2] && (e = cudaEventRecord(t[2], c->own)) != cudaSuccess) return e;
+    if ((e = launch_gather(c->p.storage, a, c->own)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(c->ev_fork, c->own)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c->side, c->ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_md_cycle(a, c->prio_high, c->side)) != cudaSuccess) return e;
+    if (t[3] && (e = cudaEventRecord(t[3], c->side)) != cudaSuccess) return e;
+  } else if (t[2]) {
+    if ((e = cudaEventRecord(t[2], c->own)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(t[3], c->own)) != cudaSuccess) return e;
   }
-  if (t0 && (e = cudaEventRecord(t0, c->own)) != cudaSuccess) return e;
+  if (t[0] && (e = cudaEventRecord(t[0], c->own)) != cudaSuccess) return e;
   if ((e = launch_lb_stream_collide(c->p.storage, c->geo, c->phys, A, B,
                                     c->N > 0 ? nullptr : c->status, c->own)) != cudaSuccess)
     return e;
-  if (t1 && (e = cudaEventRecord(t1, c->own)) != cudaSuccess) return e;
+  if (t[1] && (e = cudaEventRecord(t[1], c->own)) != cudaSuccess) return e;
   if (c->N > 0) {
     if ((e = cudaEventRecord(c->ev_join, c->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(c->own, c->ev_join, 0)) != cudaSuccess) return e;
+    if (t[4] && (e = cudaEventRecord(t[4], c->own)) != cudaSuccess) return e;
     if ((e = launch_spread(c->p.storage, c->geo, c->chain.sp_node, c->chain.sp_w, c->chain.J, c->N,
                            8 * c->N, B, c->status, c->own)) != cudaSuccess)
       return e;
+    if (t[5] && (e = cudaEventRecord(t[5], c->own)) != cudaSuccess) return e;
+  } else if (t[4]) {
+    if ((e = cudaEventRecord(t[4], c->own)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(t[5], c->own)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -307,7 +327,7 @@ cudaError_t capture(lbmd_ctx *c, int start, int nsteps, cudaGraphExec_t *out) {
     return e2;
   }
   if (e != cudaSuccess) return e;
-  e = cudaGraphInstantiate(out, g, 0);
+  e = cudaGraphInstantiate(out, g, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(g);
   return e;
 }
@@ -397,7 +417,9 @@ int lbmd_create(const lbmd_params *params, void *dev_workspace, size_t bytes, vo
   };
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
-  if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
+  int prio_least = 0;
+  if ((e = cudaDeviceGetStreamPriorityRange(&prio_least, &c->prio_high)) != cudaSuccess) return bail(e, "priority range");
+  if ((e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, c->prio_high)) != cudaSuccess) return bail(e, "stream");
   for (cudaEvent_t *ev : {&c->ev_in, &c->ev_out, &c->ev_fork, &c->ev_join})
     if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
 
@@ -483,13 +505,19 @@ int lbmd_create(const lbmd_params *params, void *dev_workspace, size_t bytes, vo
   a.J = (float4 *)(c->ws + L.J);
   a.sp_node = (int *)(c->ws + L.sp_node);
   a.sp_w = (float *)(c->ws + L.sp_w);
-  a.b0 = (const float *)(c->ws + L.b0);
+  a.b0 = (const double *)(c->ws + L.b0);
+  a.nl_cnt = (int *)(c->ws + L.nl_cnt);
+  a.wl_cnt = (int *)(c->ws + L.wl_cnt);
+  a.nl_list = (short *)(c->ws + L.nl_list);
+  a.wl_list = (float4 *)(c->ws + L.wl_list);
+  a.nl_ref = (float4 *)(c->ws + L.nl_ref);
+  a.lam = (float *)(c->ws + L.lam);
   a.status = c->status;
   const int N = p.n_beads;
   // host staging kept alive until the stream synchronisation below
   std::vector<float4> hp(std::max(N, 1)), hl(std::max(N, 1)), hv(std::max(N, 1)),
       hz(std::max(N, 1), make_float4(0, 0, 0, 0));
-  std::vector<float> hb(std::max(N - 1, 1), 0.f);
+  std::vector<double> hb(std::max(N - 1, 1), 0.0);
   if (N > 0) {
     a.ox = (int)std::floor(p.init_pos[0]);
     a.oy = (int)std::floor(p.init_pos[1]);
@@ -506,15 +534,19 @@ int lbmd_create(const lbmd_params *params, void *dev_workspace, size_t bytes, vo
                          : make_float4(0, 0, 0, 0);
     }
     for (int k = 0; k + 1 < N; ++k)
-      hb[k] = (float)(p.n_constraints > 0 ? p.bond_len[k] : p.bond_length);
+      hb[k] = p.n_constraints > 0 ? p.bond_len[k] : p.bond_length;
     if ((e = cudaMemcpyAsync(a.pos, hp.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(e, "upload");
     if ((e = cudaMemcpyAsync(a.pos_lo, hl.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(e, "upload");
     if ((e = cudaMemcpyAsync(a.vel, hv.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(e, "upload");
     if ((e = cudaMemcpyAsync(a.ui, hz.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(e, "upload");
     if ((e = cudaMemcpyAsync(a.J, hz.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(e, "upload");
-    if ((e = cudaMemcpyAsync(c->ws + L.b0, hb.data(), hb.size() * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(e, "upload");
+    if ((e = cudaMemcpyAsync(c->ws + L.b0, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(e, "upload");
     if ((e = cudaMemsetAsync(a.sp_node, 0xff, 8 * (size_t)N * sizeof(int), s)) != cudaSuccess) return bail(e, "memset");
-    if ((e = md_prepare(p.storage, N)) != cudaSuccess) return bail(e, "md attributes");
+    if ((e = cudaMemsetAsync(a.nl_cnt, 0, (size_t)N * sizeof(int), s)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemsetAsync(a.wl_cnt, 0, (size_t)N * sizeof(int), s)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemsetAsync(a.lam, 0, (size_t)N * sizeof(float), s)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemcpyAsync(a.nl_ref, hp.data(), N * sizeof(float4), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(e, "upload");
+    if ((e = md_prepare(N)) != cudaSuccess) return bail(e, "md attributes");
   }
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(e, "create sync");
   *out = c;
@@ -664,24 +696,44 @@ int lbmd_set_kernel_timing(lbmd_ctx *c, int enable) {
   CK(c, cudaStreamSynchronize(c->own));
   c->timing = enable ? 1 : 0;
   c->tev_used = 0;
-  c->timed_ms = 0;
+  c->timed_ms[0] = c->timed_ms[1] = c->timed_ms[2] = 0;
   c->timed_count = 0;
+  return LBMD_OK;
+}
+
+static int collect_times(lbmd_ctx *c) {
+  CK(c, cudaStreamSynchronize(c->own));
+  CK(c, cudaStreamSynchronize(c->side));
+  for (size_t k = 0; k + 5 < c->tev_used; k += 6) {
+    for (int q = 0; q < 3; ++q) {
+      float ms = 0.f;
+      CK(c, cudaEventElapsedTime(&ms, c->tev[k + 2 * q], c->tev[k + 2 * q + 1]));
+      c->timed_ms[q] += ms;
+    }
+    c->timed_count += 1;
+  }
+  c->tev_used = 0;
   return LBMD_OK;
 }
 
 int lbmd_lb_kernel_time(lbmd_ctx *c, double *total_ms, int64_t *launches) {
   int rc = check_ctx(c);
   if (rc) return rc;
-  CK(c, cudaStreamSynchronize(c->own));
-  for (size_t k = 0; k + 1 < c->tev_used; k += 2) {
-    float ms = 0.f;
-    CK(c, cudaEventElapsedTime(&ms, c->tev[k], c->tev[k + 1]));
-    c->timed_ms += ms;
-    c->timed_count += 1;
-  }
-  c->tev_used = 0;
-  if (total_ms) *total_ms = c->timed_ms;
+  if ((rc = collect_times(c))) return rc;
+  if (total_ms) *total_ms = c->timed_ms[0];
   if (launches) *launches = c->timed_count;
+  return LBMD_OK;
+}
+
+int lbmd_kernel_times(lbmd_ctx *c, double *lb_ms, double *md_ms, double *spread_ms,
+                      int64_t *steps) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if ((rc = collect_times(c))) return rc;
+  if (lb_ms) *lb_ms = c->timed_ms[0];
+  if (md_ms) *md_ms = c->timed_ms[1];
+  if (spread_ms) *spread_ms = c->timed_ms[2];
+  if (steps) *steps = c->timed_count;
   return LBMD_OK;
 }
 

@@ -18,7 +18,14 @@ struct DevStatus {
   int state;             // LBMD_RUNNING, ...
   int shake_fail;        // LB steps whose constraint solve hit the iteration cap
   int newton_iters;      // Newton iterations of the last LB step (all substeps)
+  int nl_builds;         // neighbour-list builds so far (0: none yet)
+  int nl_ok;             // 1 if the current lists hold every pair (no overflow)
 };
+
+// Neighbour-list capacities per bead: bead partners and solid nodes within
+// r_c + skin (a sphere of radius 2.83 holds at most ~100 lattice nodes).
+constexpr int kMaxPairs = 48;
+constexpr int kMaxWall = 128;
 
 // Lattice geometry as the kernels see it.
 struct LbGeom {
@@ -56,14 +63,19 @@ struct ChainArgs {
   float4 *ui, *J;           // interpolated u and impulse of the last step
   int *sp_node;             // [8N] grid node of each transfer weight, -1 none
   float *sp_w;              // [8N] renormalised transfer weights
-  const float *b0;          // [N-1] bond lengths
+  const double *b0;         // [N-1] bond lengths
+  int *nl_cnt, *wl_cnt;     // [N] list lengths
+  short *nl_list;           // [N][kMaxPairs] partner beads
+  float4 *wl_list;          // [N][kMaxWall] solid nodes (local frame)
+  float4 *nl_ref;           // [N] positions at the last list build
+  float *lam;               // [N] SHAKE multipliers of the last substep
   DevStatus *status;
 };
 
 size_t md_smem_bytes(int N);
 int md_threads(int N);
 // Opt the MD kernel into the dynamic shared memory a chain of N beads needs.
-cudaError_t md_prepare(int storage, int N);
+cudaError_t md_prepare(int N);
 
 // Launchers (each returns the launch error, if any).
 cudaError_t launch_lb_stream_collide(int storage, const LbGeom &g, const LbPhys &ph,
@@ -78,7 +90,8 @@ cudaError_t launch_read_moments(int storage, const LbGeom &g, const LbPhys &ph,
 cudaError_t launch_read_pulled(int storage, const LbGeom &g, float rho0, const void *src,
                                long long z0, long long nzc, float *f, long long fstride,
                                cudaStream_t s);
-cudaError_t launch_md_cycle(int storage, const ChainArgs &a, cudaStream_t s);
+cudaError_t launch_gather(int storage, const ChainArgs &a, cudaStream_t s);
+cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s);
 cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, const float *sp_w,
                           const float4 *J, int N, int nw, void *dst, DevStatus *bump,
                           cudaStream_t s);

@@ -32,7 +32,7 @@ DEFAULTS = dict(
     tau=1.0, rho0=1.0, body_force=(0.0, 0.0, 0.0),
     bead_mass=1.0, gamma=0.1, kT=1e-4, lj_sigma=1.8, lj_eps=1.0,
     kappa_phi=0.0, f_drive=0.02, bond_len=1.2,
-    shake_tol=1e-6, shake_max_iter=12, init_tg_amp=0.0, seed=0,
+    shake_tol=1e-8, shake_max_iter=12, init_tg_amp=0.0, seed=0,
 )
 IGNORED_KEYS = {"hydrodynamics", "bonds"}  # oracle-only keys
 
@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True):
     L.lbmd_solver_stats.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.lbmd_set_kernel_timing.argtypes = [P, C.c_int]
     L.lbmd_lb_kernel_time.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.lbmd_kernel_times.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.lbmd_destroy.argtypes = [P]
     L.lbmd_strerror.argtypes = [C.c_int]
     L.lbmd_strerror.restype = C.c_char_p
@@ -99,7 +101,7 @@ def load(build_if_missing: bool = True):
     for name in ("lbmd_workspace_size", "lbmd_create", "lbmd_step", "lbmd_read_fields",
                  "lbmd_read_populations", "lbmd_read_beads", "lbmd_read_bead_aux", "lbmd_status",
                  "lbmd_set_kernel_timing", "lbmd_lb_kernel_time", "lbmd_destroy", "lbmd_version",
-                 "lbmd_solver_stats"):
+                 "lbmd_solver_stats", "lbmd_kernel_times"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -221,6 +223,13 @@ def lbmd_lb_kernel_time(ctx):
     return ms.value, n.value
 
 
+def lbmd_kernel_times(ctx) -> dict:
+    lb, md, sp, n = C.c_double(), C.c_double(), C.c_double(), C.c_int64()
+    _check(load().lbmd_kernel_times(ctx, C.byref(lb), C.byref(md), C.byref(sp), C.byref(n)),
+           "lbmd_kernel_times")
+    return dict(lb_ms=lb.value, md_ms=md.value, spread_ms=sp.value, steps=n.value)
+
+
 def lbmd_destroy(ctx) -> None:
     _check(load().lbmd_destroy(ctx), "lbmd_destroy")
 
@@ -319,3 +328,6 @@ class Simulation:
 
     def lb_kernel_time(self):
         return lbmd_lb_kernel_time(self.ctx)
+
+    def kernel_times(self) -> dict:
+        return lbmd_kernel_times(self.ctx)

