@@ -41,7 +41,7 @@ int md_threads(int N) { return (N + 31) / 32 * 32; }
 // Shared memory of the MD block: positions (hi, lo), displacements, bond
 // vectors, velocities, the tridiagonal work arrays and the pair lists.
 size_t md_smem_bytes(int N) {
-  return (size_t)N * (5 * sizeof(float4) + 9 * sizeof(float) + kMaxPairs * sizeof(short));
+  return (size_t)N * (5 * sizeof(float4) + sizeof(float) + kMaxPairs * sizeof(short));
 }
 
 // Double-float helpers: a coordinate is hi + lo with |lo| <= ulp(hi) / 2.
@@ -65,132 +65,140 @@ __device__ __forceinline__ void cell_frac_hl(float hi, float lo, int origin, int
   cell = wrapi(origin + (int)fl, n);
 }
 
-// Tridiagonal solve A x = D over rows 0..n-1 (sub-diagonal a_i, diagonal
-// b_i, super-diagonal c_i; a_0 = c_{n-1} = 0) by one warp, partition method:
-// lane k owns rows [k m, k m + m) with m = max(2, ceil(n / 32)).  A downward
-// sweep expresses each row through the partition's first unknown, a backward
-// sweep writes every interior unknown as g + h x_first + k x_last, and the
-// first/last rows of all partitions form a 2P-row tridiagonal system; folding
-// each lane's first row into its last row leaves one row per lane, solved by
-// cyclic reduction with shuffles.  No block barrier inside; the caller
-// publishes the rows in shared memory before and reads X after.
-__device__ void warp_tri_solve(int n, const float *A, const float *B, const float *C,
-                               const float *D, float *X, float *G, float *H, float *K) {
-  const int lane = threadIdx.x & 31;
-  const int m = max(2, (n + 31) / 32);
-  const int P = (n + m - 1) / m;
-  const int s = lane * m;
-  const int e = min(n, s + m) - 1;
-  const bool active = lane < P;
-  float a1 = 0.f, b1 = 1.f, c1 = 0.f, d1 = 0.f;  // first row of the partition
-  float a2 = 0.f, b2 = 1.f, c2 = 0.f, d2 = 0.f;  // last row
-  if (active) {
-    if (e == s) {  // one-row partition: only the last one can be this short
-      a1 = A[s];
-      b1 = B[s];
-      d1 = D[s];
-      a2 = -1.f;  // x_last - x_first = 0
-    } else {
-      // downward: row i as L_i x_s + Bd_i x_i + c_i x_{i+1} = Dd_i, i = s+1..e
-      float L = A[s + 1], Bd = B[s + 1], Dd = D[s + 1];
-      H[s + 1] = L;
-      K[s + 1] = Bd;
-      G[s + 1] = Dd;
-      for (int i = s + 2; i <= e; ++i) {
-        const float f = A[i] * __frcp_rn(Bd);
-        L = -f * L;
-        Bd = B[i] - f * C[i - 1];
-        Dd = D[i] - f * Dd;
-        H[i] = L;
-        K[i] = Bd;
-        G[i] = Dd;
-      }
-      a2 = L;
-      b2 = Bd;
-      c2 = C[e];
-      d2 = Dd;
-      // backward: x_i = g_i + h_i x_s + k_i x_e, i = e-1 .. s+1
-      float g = 0.f, h = 0.f, k = 1.f;
-      for (int i = e - 1; i >= s + 1; --i) {
-        const float inv = __frcp_rn(K[i]);
-        const float gi = (G[i] - C[i] * g) * inv;
-        const float hi = (-H[i] - C[i] * h) * inv;
-        const float ki = (-C[i] * k) * inv;
-        G[i] = gi;
-        H[i] = hi;
-        K[i] = ki;
-        g = gi;
-        h = hi;
-        k = ki;
-      }
-      a1 = A[s];
-      b1 = B[s] + C[s] * h;
-      c1 = C[s] * k;
-      d1 = D[s] - C[s] * g;
-    }
+// 2x2 matrices for the interface system of the tridiagonal solve.
+struct M2 {
+  float a, b, c, d;  // [[a, b], [c, d]]
+};
+__device__ __forceinline__ M2 mmul(M2 x, M2 y) {
+  return M2{x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c,
+            x.c * y.b + x.d * y.d};
+}
+__device__ __forceinline__ M2 madd(M2 x, M2 y) { return M2{x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d}; }
+__device__ __forceinline__ M2 minv(M2 x) {
+  const float r = 1.0f / (x.a * x.d - x.b * x.c);
+  return M2{x.d * r, -x.b * r, -x.c * r, x.a * r};
+}
+__device__ __forceinline__ M2 mshfl_up(M2 x, int s) {
+  return M2{__shfl_up_sync(0xffffffffu, x.a, s), __shfl_up_sync(0xffffffffu, x.b, s),
+            __shfl_up_sync(0xffffffffu, x.c, s), __shfl_up_sync(0xffffffffu, x.d, s)};
+}
+__device__ __forceinline__ M2 mshfl_down(M2 x, int s) {
+  return M2{__shfl_down_sync(0xffffffffu, x.a, s), __shfl_down_sync(0xffffffffu, x.b, s),
+            __shfl_down_sync(0xffffffffu, x.c, s), __shfl_down_sync(0xffffffffu, x.d, s)};
+}
+
+// Tridiagonal solve over rows 0..n-1 of the block (row i held by thread i:
+// a x_{i-1} + b x_i + c x_{i+1} = d, with a_0 = c_{n-1} = 0).  Every thread
+// of the block calls it; returns x_i and, in x_prev, x_{i-1}.
+//
+// SPIKE-type partition by warps: each warp reduces its 32 rows by cyclic
+// reduction over lane shuffles, for the right-hand side and for the two
+// coupling columns to the neighbouring warps (the "spikes" v and w), giving
+// x_i = y_i - v_i x_last(prev warp) - w_i x_first(next warp).  The first and
+// last unknowns of neighbouring warps form a block tridiagonal system with
+// 2x2 blocks, one block row per warp boundary, which warp 0 solves by block
+// cyclic reduction.  Two block barriers, none when n <= 32.
+__device__ float spike_tri_solve(int n, float a, float b, float c, float d, float &x_prev) {
+  __shared__ float sh_y[6 * 32];  // per warp: y, v, w of its first and last row
+  __shared__ float sh_x[64];      // x of the last row [0, 32) and first row [32, 64) per warp
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int nch = (n + 31) >> 5;
+  if (t >= n) {
+    a = 0.f;
+    b = 1.f;
+    c = 0.f;
+    d = 0.f;
   }
-  // fold: eliminate x_first(k) and x_first(k+1) from the last row of k
-  float a1n = __shfl_down_sync(0xffffffffu, a1, 1), b1n = __shfl_down_sync(0xffffffffu, b1, 1);
-  float c1n = __shfl_down_sync(0xffffffffu, c1, 1), d1n = __shfl_down_sync(0xffffffffu, d1, 1);
-  if (lane + 1 >= P) {
-    a1n = 0.f;
-    b1n = 1.f;
-    c1n = 0.f;
-    d1n = 0.f;
-  }
-  float al = 0.f, be = 1.f, ga = 0.f, de = 0.f;
-  if (active) {
-    const float r1 = __frcp_rn(b1), r1n = __frcp_rn(b1n);
-    al = -a2 * a1 * r1;
-    be = b2 - a2 * c1 * r1 - c2 * a1n * r1n;
-    ga = -c2 * c1n * r1n;
-    de = d2 - a2 * d1 * r1 - c2 * d1n * r1n;
-  }
-  // cyclic reduction on the P last-row unknowns (identity rows beyond P)
+  float al = lane == 0 ? 0.f : a, be = b, ga = lane == 31 ? 0.f : c;
+  float r0 = d, r1 = lane == 0 ? a : 0.f, r2 = lane == 31 ? c : 0.f;
 #pragma unroll
-  for (int st = 1; st < 32; st <<= 1) {
-    const float am = __shfl_up_sync(0xffffffffu, al, st), bm = __shfl_up_sync(0xffffffffu, be, st);
-    const float gm = __shfl_up_sync(0xffffffffu, ga, st), dm = __shfl_up_sync(0xffffffffu, de, st);
-    const float ap = __shfl_down_sync(0xffffffffu, al, st), bp = __shfl_down_sync(0xffffffffu, be, st);
-    const float gp = __shfl_down_sync(0xffffffffu, ga, st), dp = __shfl_down_sync(0xffffffffu, de, st);
-    const bool hm = lane >= st, hp = lane + st < 32;
+  for (int s = 1; s < 32; s <<= 1) {
+    const float am = __shfl_up_sync(0xffffffffu, al, s), bm = __shfl_up_sync(0xffffffffu, be, s);
+    const float gm = __shfl_up_sync(0xffffffffu, ga, s);
+    const float r0m = __shfl_up_sync(0xffffffffu, r0, s), r1m = __shfl_up_sync(0xffffffffu, r1, s);
+    const float r2m = __shfl_up_sync(0xffffffffu, r2, s);
+    const float ap = __shfl_down_sync(0xffffffffu, al, s), bp = __shfl_down_sync(0xffffffffu, be, s);
+    const float gp = __shfl_down_sync(0xffffffffu, ga, s);
+    const float r0p = __shfl_down_sync(0xffffffffu, r0, s), r1p = __shfl_down_sync(0xffffffffu, r1, s);
+    const float r2p = __shfl_down_sync(0xffffffffu, r2, s);
+    const bool hm = lane >= s, hp = lane + s < 32;
     const float k1 = hm ? al * __frcp_rn(bm) : 0.f;
     const float k2 = hp ? ga * __frcp_rn(bp) : 0.f;
-    const float nal = hm ? -k1 * am : 0.f;
-    const float nga = hp ? -k2 * gp : 0.f;
-    be = be - (hm ? k1 * gm : 0.f) - (hp ? k2 * ap : 0.f);
-    de = de - (hm ? k1 * dm : 0.f) - (hp ? k2 * dp : 0.f);
+    const float nal = hm ? -k1 * am : 0.f, nga = hp ? -k2 * gp : 0.f;
+    be = be - k1 * gm - k2 * ap;
+    r0 = r0 - k1 * r0m - k2 * r0p;
+    r1 = r1 - k1 * r1m - k2 * r1p;
+    r2 = r2 - k1 * r2m - k2 * r2p;
     al = nal;
     ga = nga;
   }
-  const float xl = de / be;
-  const float xlm = __shfl_up_sync(0xffffffffu, xl, 1);
-  if (active) {
-    const float xf = (d1 - (lane > 0 ? a1 * xlm : 0.f) - c1 * xl) / b1;
-    X[s] = xf;
-    if (e != s) {
-      X[e] = xl;
-      for (int i = s + 1; i < e; ++i) X[i] = G[i] + H[i] * xf + K[i] * xl;
+  const float ib = 1.0f / be;
+  const float y = r0 * ib, v = r1 * ib, sw = r2 * ib;
+  if (nch > 1) {
+    if (lane == 0 && w < nch) {
+      sh_y[6 * w] = y;
+      sh_y[6 * w + 1] = v;
+      sh_y[6 * w + 2] = sw;
     }
+    if (lane == 31 && w < nch) {
+      sh_y[6 * w + 3] = y;
+      sh_y[6 * w + 4] = v;
+      sh_y[6 * w + 5] = sw;
+    }
+    __syncthreads();
+    if (w == 0) {
+      // block row k: unknowns (x_last(k), x_first(k+1)) at the boundary of
+      // warps k and k+1; rows beyond nch-2 are identity rows
+      M2 L{0.f, 0.f, 0.f, 0.f}, D{1.f, 0.f, 0.f, 1.f}, U{0.f, 0.f, 0.f, 0.f};
+      float q0 = 0.f, q1 = 0.f;
+      if (lane < nch - 1) {
+        D.b = sh_y[6 * lane + 5];        // w of the last row of warp k
+        D.c = sh_y[6 * (lane + 1) + 1];  // v of the first row of warp k+1
+        L.a = sh_y[6 * lane + 4];        // v of the last row of warp k
+        U.d = sh_y[6 * (lane + 1) + 2];  // w of the first row of warp k+1
+        q0 = sh_y[6 * lane + 3];
+        q1 = sh_y[6 * (lane + 1)];
+      }
+#pragma unroll
+      for (int s = 1; s < 32; s <<= 1) {
+        const M2 Lm = mshfl_up(L, s), Dm = mshfl_up(D, s), Um = mshfl_up(U, s);
+        const float q0m = __shfl_up_sync(0xffffffffu, q0, s), q1m = __shfl_up_sync(0xffffffffu, q1, s);
+        const M2 Lp = mshfl_down(L, s), Dp = mshfl_down(D, s), Up = mshfl_down(U, s);
+        const float q0p = __shfl_down_sync(0xffffffffu, q0, s), q1p = __shfl_down_sync(0xffffffffu, q1, s);
+        M2 al2{0.f, 0.f, 0.f, 0.f}, ga2{0.f, 0.f, 0.f, 0.f};
+        if (lane >= s) {
+          const M2 t2 = mmul(L, minv(Dm));
+          al2 = M2{-t2.a, -t2.b, -t2.c, -t2.d};
+        }
+        if (lane + s < 32) {
+          const M2 t2 = mmul(U, minv(Dp));
+          ga2 = M2{-t2.a, -t2.b, -t2.c, -t2.d};
+        }
+        const M2 nL = mmul(al2, Lm), nU = mmul(ga2, Up);
+        D = madd(D, madd(mmul(al2, Um), mmul(ga2, Lp)));
+        const float nq0 = q0 + al2.a * q0m + al2.b * q1m + ga2.a * q0p + ga2.b * q1p;
+        const float nq1 = q1 + al2.c * q0m + al2.d * q1m + ga2.c * q0p + ga2.d * q1p;
+        L = nL;
+        U = nU;
+        q0 = nq0;
+        q1 = nq1;
+      }
+      const M2 Di = minv(D);
+      if (lane < nch - 1) {
+        sh_x[lane] = Di.a * q0 + Di.b * q1;           // x_last of warp k
+        sh_x[32 + lane + 1] = Di.c * q0 + Di.d * q1;  // x_first of warp k+1
+      }
+    }
+    __syncthreads();
   }
-}
-
-// Every thread of the block calls this: row i (< n) of the system comes from
-// thread i, the solution x_i goes back to thread i.
-__device__ __forceinline__ float block_tri_solve(int n, float a, float b, float c, float d,
-                                                 float *tri, float *X, int N) {
-  const int i = threadIdx.x;
-  float *A = tri, *B = tri + N, *C = tri + 2 * N, *D = tri + 3 * N;
-  if (i < n) {
-    A[i] = a;
-    B[i] = b;
-    C[i] = c;
-    D[i] = d;
+  float x = y;
+  if (nch > 1) {
+    if (w > 0 && w < nch) x -= v * sh_x[w - 1];
+    if (w + 1 < nch) x -= sw * sh_x[32 + w + 1];
   }
-  __syncthreads();
-  if (i < 32) warp_tri_solve(n, A, B, C, D, X, tri + 4 * N, tri + 5 * N, tri + 6 * N);
-  __syncthreads();
-  return i < n ? X[i] : 0.f;
+  const float xu = __shfl_up_sync(0xffffffffu, x, 1);
+  x_prev = lane > 0 ? xu : (w > 0 && w < nch && nch > 1 ? sh_x[w - 1] : 0.f);
+  return x;
 }
 
 // Eq. 2 truncated at 2^(1/6) sigma: adds -dV/dd for separation d.
@@ -402,9 +410,7 @@ __global__ void __launch_bounds__(BLOCK) k_md_cycle(ChainArgs a) {
   float4 *s_t = s_rl + N;     // displacement of the substep
   float4 *s_b = s_t + N;      // bond vectors
   float4 *s_v = s_b + N;      // velocities (RATTLE)
-  float *tri = (float *)(s_v + N);  // 7N: tridiagonal rows and work arrays
-  float *s_x = tri + 7 * N;         // N: tridiagonal solution
-  float *s_lam = s_x + N;           // N: SHAKE multipliers of the last substep
+  float *s_lam = (float *)(s_v + N);  // N: SHAKE multipliers of the last substep
   short *s_nl = (short *)(s_lam + N);  // [kMaxPairs][N] pair lists, column per bead
 
   const long long step = a.status->step;
@@ -515,14 +521,15 @@ __global__ void __launch_bounds__(BLOCK) k_md_cycle(ChainArgs a) {
           break;
         }
         ++newton_total;
-        block_tri_solve(N - 1, sub, diag, sup, -G, tri, s_x, N);
+        float xm;
+        const float x = spike_tri_solve(N - 1, sub, diag, sup, -G, xm);
         if (bead) {
           F3 dd = f3(s_t[i]);
           if (i < N - 1) {
-            dd = dd + (s_x[i] * im) * f3(s_b[i]);
-            lam += s_x[i];
+            dd = dd + (x * im) * f3(s_b[i]);
+            lam += x;
           }
-          if (i > 0) dd = dd - (s_x[i - 1] * im) * f3(s_b[i - 1]);
+          if (i > 0) dd = dd - (xm * im) * f3(s_b[i - 1]);
           s_t[i] = f4(dd);
         }
         __syncthreads();
@@ -553,10 +560,11 @@ __global__ void __launch_bounds__(BLOCK) k_md_cycle(ChainArgs a) {
         if (i > 0) sub = im * dot(dnew, f3(s_b[i - 1]));
         if (i < N - 2) sup = im * dot(dnew, f3(s_b[i + 1]));
       }
-      block_tri_solve(N - 1, sub, diag, sup, -rhs, tri, s_x, N);
+      float mum;
+      const float mu = spike_tri_solve(N - 1, sub, diag, sup, -rhs, mum);
       if (bead) {
-        if (i < N - 1) v = v + (s_x[i] * im) * f3(s_b[i]);
-        if (i > 0) v = v - (s_x[i - 1] * im) * f3(s_b[i - 1]);
+        if (i < N - 1) v = v + (mu * im) * f3(s_b[i]);
+        if (i > 0) v = v - (mum * im) * f3(s_b[i - 1]);
       }
     }
     // every read of s_rh / s_rl of this substep precedes a barrier of the

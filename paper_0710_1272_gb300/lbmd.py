@@ -32,7 +32,7 @@ DEFAULTS = dict(
     tau=1.0, rho0=1.0, body_force=(0.0, 0.0, 0.0),
     bead_mass=1.0, gamma=0.1, kT=1e-4, lj_sigma=1.8, lj_eps=1.0,
     kappa_phi=0.0, f_drive=0.02, bond_len=1.2,
-    shake_tol=1e-8, shake_max_iter=12, init_tg_amp=0.0, seed=0,
+    shake_tol=1e-6, shake_max_iter=12, init_tg_amp=0.0, seed=0,
 )
 IGNORED_KEYS = {"hydrodynamics", "bonds"}  # oracle-only keys
 
