@@ -75,7 +75,7 @@ __device__ __forceinline__ M2 mmul(M2 x, M2 y) {
 }
 __device__ __forceinline__ M2 madd(M2 x, M2 y) { return M2{x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d}; }
 __device__ __forceinline__ M2 minv(M2 x) {
-  const float r = 1.0f / (x.a * x.d - x.b * x.c);
+  const float r = __frcp_rn(x.a * x.d - x.b * x.c);
   return M2{x.d * r, -x.b * r, -x.c * r, x.a * r};
 }
 __device__ __forceinline__ M2 mshfl_up(M2 x, int s) {
@@ -159,19 +159,22 @@ __device__ float spike_tri_solve(int n, float a, float b, float c, float d, floa
         q0 = sh_y[6 * lane + 3];
         q1 = sh_y[6 * (lane + 1)];
       }
-#pragma unroll
-      for (int s = 1; s < 32; s <<= 1) {
-        const M2 Lm = mshfl_up(L, s), Dm = mshfl_up(D, s), Um = mshfl_up(U, s);
+      // block cyclic reduction over the nch - 1 boundary rows; each lane
+      // inverts its own diagonal block and the neighbours' inverses arrive by
+      // shuffle
+      for (int s = 1; s < nch - 1; s <<= 1) {
+        const M2 Di = minv(D);
+        const M2 Lm = mshfl_up(L, s), Dim = mshfl_up(Di, s), Um = mshfl_up(U, s);
         const float q0m = __shfl_up_sync(0xffffffffu, q0, s), q1m = __shfl_up_sync(0xffffffffu, q1, s);
-        const M2 Lp = mshfl_down(L, s), Dp = mshfl_down(D, s), Up = mshfl_down(U, s);
+        const M2 Lp = mshfl_down(L, s), Dip = mshfl_down(Di, s), Up = mshfl_down(U, s);
         const float q0p = __shfl_down_sync(0xffffffffu, q0, s), q1p = __shfl_down_sync(0xffffffffu, q1, s);
         M2 al2{0.f, 0.f, 0.f, 0.f}, ga2{0.f, 0.f, 0.f, 0.f};
         if (lane >= s) {
-          const M2 t2 = mmul(L, minv(Dm));
+          const M2 t2 = mmul(L, Dim);
           al2 = M2{-t2.a, -t2.b, -t2.c, -t2.d};
         }
         if (lane + s < 32) {
-          const M2 t2 = mmul(U, minv(Dp));
+          const M2 t2 = mmul(U, Dip);
           ga2 = M2{-t2.a, -t2.b, -t2.c, -t2.d};
         }
         const M2 nL = mmul(al2, Lm), nU = mmul(ga2, Up);
