@@ -53,8 +53,11 @@ __device__ __forceinline__ void collide19(float h[kQ], const LbPhys &ph) {
   }
 }
 
-template <int S, int FORCING>
-__global__ void __launch_bounds__(32 * kRowsPerBlock)
+// Six 256-thread blocks per SM (40 registers): the occupancy that measured
+// fastest for this kernel; it is HBM-bound and needs the loads of many warps
+// in flight.
+template <int S, int FORCING, typename I>
+__global__ void __launch_bounds__(32 * kRowsPerBlock, 6)
     k_stream_collide(LbGeom g, LbPhys ph, const typename Store<S>::T *__restrict__ src,
                      typename Store<S>::T *__restrict__ dst, DevStatus *bump) {
   using St = Store<S>;
@@ -63,31 +66,39 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock)
   const int z = blockIdx.z;
   if (bump != nullptr && x == 0 && y == 0 && z == 0) bump->step += 1;
   if (x >= g.nx || y >= g.ny) return;
-  const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
+  const I self = ((I)z * g.ny + y) * g.nx + x;
   float h[kQ];
   if (tile_is_near(g, x, y, z)) {
     if (solid_at(g.solid, g.ntx, g.ny, x, y, z)) return;
-    pull19<S, true>(g, src, x, y, z, h);
+    pull19<S, true, I>(g, src, x, y, z, h);
   } else {
-    pull19<S, false>(g, src, x, y, z, h);
+    pull19<S, false, I>(g, src, x, y, z, h);
   }
   collide19<FORCING>(h, ph);
-  const size_t Vp = (size_t)g.Vp;
+  const I Vp = (I)g.Vp;
 #pragma unroll
-  for (int p = 0; p < kQ; ++p) St::store(dst + (size_t)p * Vp + self, h[p]);
+  for (int p = 0; p < kQ; ++p) St::store(dst + (I)p * Vp + self, h[p]);
 }
 
-template <int S>
+template <int S, typename I>
 static cudaError_t lb_launch(const LbGeom &g, const LbPhys &ph, const void *src, void *dst,
                              DevStatus *bump, cudaStream_t s) {
   using T = typename Store<S>::T;
   dim3 block(32, kRowsPerBlock);
   dim3 grid(g.ntx, (g.ny + kRowsPerBlock - 1) / kRowsPerBlock, g.nz);
   if (ph.forcing == LBMD_FORCING_GUO)
-    k_stream_collide<S, LBMD_FORCING_GUO><<<grid, block, 0, s>>>(g, ph, (const T *)src, (T *)dst, bump);
+    k_stream_collide<S, LBMD_FORCING_GUO, I><<<grid, block, 0, s>>>(g, ph, (const T *)src, (T *)dst, bump);
   else
-    k_stream_collide<S, LBMD_FORCING_PAPER><<<grid, block, 0, s>>>(g, ph, (const T *)src, (T *)dst, bump);
+    k_stream_collide<S, LBMD_FORCING_PAPER, I><<<grid, block, 0, s>>>(g, ph, (const T *)src, (T *)dst, bump);
   return cudaGetLastError();
+}
+
+template <int S>
+static cudaError_t lb_launch(const LbGeom &g, const LbPhys &ph, const void *src, void *dst,
+                             DevStatus *bump, cudaStream_t s) {
+  // 32-bit offsets when every population index fits
+  if ((long long)kQ * g.Vp < 0x7fffffffLL) return lb_launch<S, int>(g, ph, src, dst, bump, s);
+  return lb_launch<S, size_t>(g, ph, src, dst, bump, s);
 }
 
 cudaError_t launch_lb_stream_collide(int storage, const LbGeom &g, const LbPhys &ph,

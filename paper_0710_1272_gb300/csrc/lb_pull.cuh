@@ -12,7 +12,9 @@ namespace lbmd {
 //   h_p(x) = h*_opp(p)(x)       otherwise (the population that left x towards
 //                               the solid node comes back reversed).
 // CHECK = false skips the solid test (tile known to be far from any solid).
-template <int S, bool CHECK>
+// I is the index type of the population offsets: int when 19 Vp < 2^31
+// (cheaper address arithmetic), size_t otherwise.
+template <int S, bool CHECK, typename I = size_t>
 __device__ __forceinline__ void pull19(const LbGeom &g, const typename Store<S>::T *__restrict__ src,
                                        int x, int y, int z, float h[kQ]) {
   using St = Store<S>;
@@ -20,8 +22,8 @@ __device__ __forceinline__ void pull19(const LbGeom &g, const typename Store<S>:
   const int xm = wrap_m1(x, nx), xp = wrap_p1(x, nx);
   const int ym = wrap_m1(y, ny), yp = wrap_p1(y, ny);
   const int zm = wrap_m1(z, nz), zp = wrap_p1(z, nz);
-  const size_t self = ((size_t)z * ny + y) * nx + x;
-  const size_t Vp = (size_t)g.Vp;
+  const I self = ((I)z * ny + y) * nx + x;
+  const I Vp = (I)g.Vp;
   // first every solid test (independent loads of the bitfield), then every
   // population address, so that the 19 population loads are in flight together
   uint32_t bb = 0;
@@ -40,8 +42,8 @@ __device__ __forceinline__ void pull19(const LbGeom &g, const typename Store<S>:
     const int sx = cx(p) == 1 ? xm : (cx(p) == -1 ? xp : x);
     const int sy = cy(p) == 1 ? ym : (cy(p) == -1 ? yp : y);
     const int sz = cz(p) == 1 ? zm : (cz(p) == -1 ? zp : z);
-    const size_t sidx = (size_t)p * Vp + ((size_t)sz * ny + sy) * nx + sx;
-    const size_t bidx = (size_t)opp(p) * Vp + self;
+    const I sidx = (I)p * Vp + ((I)sz * ny + sy) * nx + sx;
+    const I bidx = (I)opp(p) * Vp + self;
     h[p] = St::load(src + (((bb >> p) & 1u) ? bidx : sidx));
   }
 }

@@ -57,12 +57,21 @@ __device__ __forceinline__ F3 diff_hl(float4 ah, float4 al, float4 bh, float4 bl
   return F3{(ah.x - bh.x) + (al.x - bl.x), (ah.y - bh.y) + (al.y - bl.y),
             (ah.z - bh.z) + (al.z - bl.z)};
 }
+// Index into [0, n): one add or subtract for indices within a period of the
+// box (the common case), the integer remainder otherwise.
+__device__ __forceinline__ int wrap_near(int a, int n) {
+  if (a < 0) a += n;
+  if (a >= n) a -= n;
+  if ((unsigned)a >= (unsigned)n) a = wrapi(a, n);
+  return a;
+}
+
 // Wrapped node index and fraction of global = origin + hi + lo.
 __device__ __forceinline__ void cell_frac_hl(float hi, float lo, int origin, int n, int &cell,
                                              float &frac) {
   const float fl = floorf(hi);
   frac = (hi - fl) + lo;
-  cell = wrapi(origin + (int)fl, n);
+  cell = wrap_near(origin + (int)fl, n);
 }
 
 // 2x2 matrices for the interface system of the tridiagonal solve.
@@ -278,7 +287,7 @@ __device__ F3 bend_drive_forces(const ChainArgs &a, int i, const float4 *s_rh, c
     cell_frac_hl(rh.x, rl.x, a.ox, g.nx, c[0], sf[0]);
     cell_frac_hl(rh.y, rl.y, a.oy, g.ny, c[1], sf[1]);
     cell_frac_hl(rh.z, rl.z, a.oz, g.nz, c[2], sf[2]);
-    const int di = wrapi(c[0] - a.wall_x + g.nx / 2, g.nx) - g.nx / 2;
+    const int di = wrap_near(c[0] - a.wall_x + g.nx / 2, g.nx) - g.nx / 2;
     const float dx = (float)di + sf[0] - 0.5f * (float)(a.wall_t - 1);
     const float half = 0.5f * (float)(a.wall_t - 1) + 1.5f;
     const float ry = (float)c[1] + sf[1], rz = (float)c[2] + sf[2];
@@ -446,7 +455,7 @@ __global__ void __launch_bounds__(BLOCK) k_md_cycle(ChainArgs a) {
   const float dt = a.dt, m = a.mass, im = 1.0f / a.mass, idt = 1.0f / a.dt;
   const float sig_r = sqrtf(2.0f * m * a.gamma * a.kT / dt);
   const double b0 = (bead && i < N - 1 && a.has_bonds) ? a.b0[i] : 1.0;
-  const float tol = fmaxf(a.shake_tol, 1e-9f);
+  const float tol = fmaxf(a.shake_tol, 5e-7f);
   int shake_bad = 0, newton_total = 0, builds = 0;
 
   for (int k = 0; k < a.M; ++k) {  // (2) M MD substeps
@@ -484,42 +493,38 @@ __global__ void __launch_bounds__(BLOCK) k_md_cycle(ChainArgs a) {
       // positions); the Jacobian and the corrections stay in float.
       // Warm start: the multipliers of the previous substep applied along the
       // new old-bond vectors (the constraint forces change slowly).
-      double sx = 0, sy = 0, sz = 0;
       float lam = 0.f;
+      F3 sb{0.f, 0.f, 0.f};
       if (bead) {
         F3 sm{0.f, 0.f, 0.f};
         if (i > 0) sm = diff_hl(rh, rl, s_rh[i - 1], s_rl[i - 1]);
         if (i < N - 1) {
-          const float4 h1 = s_rh[i + 1], l1 = s_rl[i + 1];
-          sx = ((double)h1.x - (double)rh.x) + ((double)l1.x - (double)rl.x);
-          sy = ((double)h1.y - (double)rh.y) + ((double)l1.y - (double)rl.y);
-          sz = ((double)h1.z - (double)rh.z) + ((double)l1.z - (double)rl.z);
-          s_b[i] = make_float4((float)sx, (float)sy, (float)sz, 0.f);
+          sb = diff_hl(s_rh[i + 1], s_rl[i + 1], rh, rl);
+          s_b[i] = f4(sb);
           lam = s_lam[i];
-          D = D + (lam * im) * F3{(float)sx, (float)sy, (float)sz};
+          D = D + (lam * im) * sb;
         }
         if (i > 0) D = D - (s_lam[i - 1] * im) * sm;
         s_t[i] = f4(D);
       }
       __syncthreads();
+      const float b02 = (float)(b0 * b0);
       for (int it = 0;; ++it) {
         float G = 0.f, diag = 1.f, sub = 0.f, sup = 0.f;
         bool ok = true;
         if (i < N - 1) {
-          const F3 sb = f3(s_b[i]);
-          const F3 dD = f3(s_t[i + 1]) - f3(s_t[i]);
-          const double dx = sx + (double)dD.x, dy = sy + (double)dD.y, dz = sz + (double)dD.z;
-          const double Gd = dx * dx + dy * dy + dz * dz - b0 * b0;
-          G = (float)Gd;
-          ok = fabs(Gd) <= (double)tol * b0 * b0;
-          const F3 d = sb + dD;
+          // old bond from the double-float positions, displacements small: the
+          // float residual is good to ~1e-7 of b0^2
+          const F3 d = sb + (f3(s_t[i + 1]) - f3(s_t[i]));
+          G = dot(d, d) - b02;
+          ok = fabsf(G) <= tol * b02;
           diag = -4.0f * im * dot(d, sb);
           if (i > 0) sub = 2.0f * im * dot(d, f3(s_b[i - 1]));
           if (i < N - 2) sup = 2.0f * im * dot(d, f3(s_b[i + 1]));
         }
         if (__syncthreads_and(ok)) break;
         if (it >= a.shake_maxit) {
-          const bool bad = (i < N - 1) && !(fabsf(G) <= 1e-3f * (float)(b0 * b0));
+          const bool bad = (i < N - 1) && !(fabsf(G) <= 1e-3f * b02);
           if (__syncthreads_or(bad)) shake_bad = 1;
           break;
         }
