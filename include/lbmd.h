@@ -203,6 +203,35 @@ int lbmd_lb_kernel_time(lbmd_ctx *ctx, double *total_ms, int64_t *launches);
 int lbmd_kernel_times(lbmd_ctx *ctx, double *lb_ms, double *md_ms, double *spread_ms,
                       int64_t *steps);
 
+/*
+ * One D3Q19 stream-collide step (pure solvent, no beads) on caller-owned
+ * populations, for callers that cannot allocate device memory: code whose
+ * device memory is fully owned by another framework's pool, code running while
+ * another thread captures a CUDA graph in global mode (cudaMalloc is then
+ * prohibited), or a real-time loop that must not call the allocator.  It needs
+ * no context and no workspace and allocates nothing.  The paper has no
+ * counterpart: this is a convenience of this library.
+ *   params:  box, wall/pore geometry, y_walls, tau, rho0, body_force, forcing;
+ *            storage must be LBMD_STORE_F32 and n_beads 0 (other fields ignored)
+ *   f_in:    device, 19*V floats [19][z][y][x], the pre-collision populations
+ *            f_p(x, t) (absolute values, not deviations); solid nodes ignored
+ *   f_out:   device, 19*V floats, receives f_p(x, t+1); solid nodes set to 0;
+ *            must not overlap f_in
+ *   cuda_stream: stream of the work (cudaStream_t; NULL = legacy default)
+ * The geometry scratch (solid bitfield + tile flags) lives in one fixed device
+ * array inside the library, 5 MiB per GPU that loads the library, held until
+ * the process exits; it limits the box to ny * nz * ceil(nx / 32) <= 2^20
+ * (e.g. 256^3).  Each call rebuilds it on the stream, so nothing carries over
+ * from the previous call, but every call shares it: calls that may overlap on
+ * the GPU (unordered streams) race and must be serialised by the caller.  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Asynchronous; errors: LBMD_EINVAL (bad parameter, f_in == f_out),
+ * LBMD_ESIZE (box beyond the scratch limit), LBMD_ECUDA.
+ */
+int lbmd_lb_step_noalloc(const lbmd_params *params, const float *f_in, float *f_out,
+                         void *cuda_stream);
+
 /* Release the context's host resources (not the caller's workspace). */
 int lbmd_destroy(lbmd_ctx *ctx);
 

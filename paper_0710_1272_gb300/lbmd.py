@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
     L.lbmd_lb_kernel_time.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.lbmd_kernel_times.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.lbmd_lb_step_noalloc.argtypes = [C.POINTER(lbmd_params), P, P, P]
     L.lbmd_destroy.argtypes = [P]
     L.lbmd_strerror.argtypes = [C.c_int]
     L.lbmd_strerror.restype = C.c_char_p
@@ -101,7 +102,7 @@ def load(build_if_missing: bool = True):
     for name in ("lbmd_workspace_size", "lbmd_create", "lbmd_step", "lbmd_read_fields",
                  "lbmd_read_populations", "lbmd_read_beads", "lbmd_read_bead_aux", "lbmd_status",
                  "lbmd_set_kernel_timing", "lbmd_lb_kernel_time", "lbmd_destroy", "lbmd_version",
-                 "lbmd_solver_stats", "lbmd_kernel_times"):
+                 "lbmd_solver_stats", "lbmd_kernel_times", "lbmd_lb_step_noalloc"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -228,6 +229,13 @@ def lbmd_kernel_times(ctx) -> dict:
     _check(load().lbmd_kernel_times(ctx, C.byref(lb), C.byref(md), C.byref(sp), C.byref(n)),
            "lbmd_kernel_times")
     return dict(lb_ms=lb.value, md_ms=md.value, spread_ms=sp.value, steps=n.value)
+
+
+def lbmd_lb_step_noalloc(params: lbmd_params, f_in_ptr: int, f_out_ptr: int, stream_ptr: int) -> None:
+    """One solvent stream-collide step on caller-owned device populations
+    (pre-collision in, pre-collision out), without any allocation."""
+    _check(load().lbmd_lb_step_noalloc(C.byref(params), C.c_void_p(f_in_ptr), C.c_void_p(f_out_ptr),
+                                       C.c_void_p(stream_ptr)), "lbmd_lb_step_noalloc")
 
 
 def lbmd_destroy(ctx) -> None:
