@@ -45,13 +45,36 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["translocation", "solvent", "poiseuille"],
+                    default="translocation")
+    ap.add_argument("--box", type=int, default=256, help="edge of the periodic solvent box")
+    ap.add_argument("--tau", type=float, default=1.0)
     return ap.parse_args()
 
 
-def workload(seed: int, storage: str):
-    p = si.paper_translocation(seed)
+def workload(seed: int, storage: str, args=None):
+    """Parameters of the timed workload (all inputs seeded and synthetic)."""
+    kind = args.workload if args is not None else "translocation"
+    if kind == "solvent":
+        # periodic box, Taylor-Green start (A = 0.01), body force 1e-6 along x
+        p = si.periodic_solvent(args.box, tau=args.tau, g=1e-6)
+        p["init_tg_amp"] = 0.01
+    elif kind == "poiseuille":
+        p = si.poiseuille_channel(256, 128, 128, tau=args.tau, g=1e-6)
+    else:
+        p = si.paper_translocation(seed)
+        p["tau"] = args.tau if args is not None else 1.0
     p["storage"] = storage
     return p
+
+
+def workload_name(p) -> str:
+    if p["n_beads"] > 0:
+        return (f"translocation {p['nx']}x{p['ny']}x{p['nz']}, wall x={p['wall_x']}, "
+                f"{p['pore_d']}x{p['pore_d']} pore, N={p['n_beads']} beads, tau={p['tau']}")
+    if p.get("y_walls"):
+        return f"Poiseuille channel {p['nx']}x{p['ny']}x{p['nz']}, walls y=0,{p['ny'] - 1}, tau={p['tau']}"
+    return f"periodic solvent {p['nx']}^3, Taylor-Green A=0.01, g=1e-6, tau={p['tau']}"
 
 
 def dist_env():
@@ -64,6 +87,18 @@ def dist_env():
 def shard_seed(base: int, rank: int) -> int:
     """Seed of the independent realisation a rank steps (weak scaling)."""
     return base + 7919 * rank
+
+
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings (the job is as slow as its
+    slowest rank); identity without a process group."""
+    if dist is None:
+        return list(values)
+    import torch
+
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
 
 
 class ClockSampler:
@@ -135,7 +170,9 @@ def cpu_baseline(p, pos, seconds: float):
 
     cores = oracle.max_threads()
     op = {k: v for k, v in p.items() if k not in ("storage", "init_tg_amp")}
-    sim = oracle.OracleSim(op, init_pos=pos)
+    init_u = (si.taylor_green_field(p["nx"], p["ny"], p["nz"], p["init_tg_amp"])
+              if p.get("init_tg_amp") else None)
+    sim = oracle.OracleSim(op, init_pos=pos, init_u=init_u)
     t0 = time.perf_counter()
     sim.step(1)
     t1 = time.perf_counter()
@@ -146,7 +183,7 @@ def cpu_baseline(p, pos, seconds: float):
     dt = time.perf_counter() - t0
     V = p["nx"] * p["ny"] * p["nz"]
     return {"value": V * n / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{n} coupled LB steps of the {p['nx']}x{p['ny']}x{p['nz']} box with "
+            "sample": f"{n} LB steps of the {p['nx']}x{p['ny']}x{p['nz']} box with "
                       f"{p['n_beads']} beads after 1 warm-up step (FP64, OpenMP)"}
 
 
@@ -154,12 +191,14 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    p = workload(0, args.storage)
-    pos = si.saw_chain(p, 0)
+    p = workload(0, args.storage, args)
+    pos = si.saw_chain(p, 0) if p["n_beads"] > 0 else None
     import oracle
 
     op = {k: v for k, v in p.items() if k not in ("storage", "init_tg_amp")}
-    sim = oracle.OracleSim(op, init_pos=pos)
+    init_u = (si.taylor_green_field(p["nx"], p["ny"], p["nz"], p["init_tg_amp"])
+              if p.get("init_tg_amp") else None)
+    sim = oracle.OracleSim(op, init_pos=pos, init_u=init_u)
     sim.step(min(args.warmup, 1))
     budget = 90.0
     t0 = time.perf_counter()
@@ -175,8 +214,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": done, "warmup": min(args.warmup, 1),
         "ms_per_step": 1e3 * dt / max(done, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "translocation 256x128x128, wall x=128, 5x5 pore, N=400 beads, tau=1",
-                   "storage": "f64 (oracle)"},
+        "config": {"workload": workload_name(p), "storage": "f64 (oracle)"},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.max_threads(),
                          "kind": "oracle",
                          "sample": f"{done} of {args.steps} requested steps (time cap {budget:.0f} s) "
@@ -200,8 +238,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     import paper_0710_1272_gb300 as lb
 
-    p = workload(shard_seed(0, rank), args.storage)
-    pos = si.saw_chain(p, shard_seed(0, rank))
+    p = workload(shard_seed(0, rank), args.storage, args)
+    pos = si.saw_chain(p, shard_seed(0, rank)) if p["n_beads"] > 0 else None
     V = p["nx"] * p["ny"] * p["nz"]
     stream = torch.cuda.Stream()
     sim = lb.Simulation(p, init_pos=pos, stream=stream)
@@ -234,12 +272,7 @@ def run_ours(args):
         barrier()
         lb_ms, lb_n = sim.lb_kernel_time()
         sim.set_kernel_timing(False)
-    ms = ev0.elapsed_time(ev1)
-    ms_direct = ev2.elapsed_time(ev3)
-    if dist is not None:
-        t = torch.tensor([ms, ms_direct], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_direct = t.tolist()
+    ms, ms_direct = max_over_ranks([ev0.elapsed_time(ev1), ev2.elapsed_time(ev3)], dist, "cuda")
     st = sim.status()
 
     # -- end to end through the public API with host buffers ------------------
@@ -251,14 +284,11 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         lb.lbmd_step(sim.ctx, 1)
-        lb.lbmd_read_beads(sim.ctx, pos_h.ctypes.data, vel_h.ctypes.data, 0)
+        if N:
+            lb.lbmd_read_beads(sim.ctx, pos_h.ctypes.data, vel_h.ctypes.data, 0)
         lb.lbmd_status(sim.ctx)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = t.item()
+    e2e_s = max_over_ranks([time.perf_counter() - t0], dist, "cuda")[0]
 
     if rank != 0:
         dist.destroy_process_group()
@@ -287,10 +317,12 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": "translocation 256x128x128, wall x=128, 5x5 pore, N=400 beads, tau=1",
-                   "storage": args.storage, "seed": shard_seed(0, rank), "parallelism":
+        "config": {"workload": workload_name(p), "storage": args.storage,
+                   "seed": shard_seed(0, rank), "parallelism":
                    "independent realisation per GPU" if world > 1 else "1 GPU",
-                   "l2": "no flush: populations 637.5 MB/step (fp32) > 129 MB L2"},
+                   "l2": (f"no flush: populations {2 * BYTES_PER_NODE[args.storage] * V / 2 / 1e6:.1f} "
+                          "MB read+written per step > 129 MB L2" if BYTES_PER_NODE[args.storage] * V > 129e6
+                          else "fits in L2: not an HBM figure")},
         "coupled_steps_per_s": world * args.steps / (ms / 1e3),
         "value_direct_launch": world * V * args.steps / (ms_direct / 1e3) / 1e6,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -299,9 +331,10 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": lb_avg_s * 1e3, "launches_timed": lb_n},
         "e2e": {"value": world * V * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
-                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": N * 48 + 24,
-                "api": "lbmd_step(1) + lbmd_read_beads(host) + lbmd_status per step"},
-        "gpu_launches": 3 * args.steps,
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": N * 48 + 48,
+                "api": ("lbmd_step(1) + lbmd_read_beads(host) + lbmd_status per step" if N
+                        else "lbmd_step(1) + lbmd_status per step")},
+        "gpu_launches": (4 if p["n_beads"] > 0 else 1) * args.steps,
         "clocks": clocks,
         "status": st,
     }
