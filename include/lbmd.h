@@ -235,6 +235,118 @@ int lbmd_lb_step_noalloc(const lbmd_params *params, const float *f_in, float *f_
 /* Release the context's host resources (not the caller's workspace). */
 int lbmd_destroy(lbmd_ctx *ctx);
 
+/* ---- ensembles of independent realisations ------------------------------
+ * The translocation statistics of Sec. III (duration histograms, the
+ * time-versus-length exponent) come from ensembles of 100-1000 realisations
+ * per chain length, each started from a different initial chain.  An
+ * ensemble context advances many independent realisations -- each with its
+ * own box, wall/pore geometry, chain, parameters and seed, all with the same
+ * storage type and forcing -- through one set of launches per LB step: the
+ * gather and the spread over every bead of every realisation, one MD block
+ * per chain (chains grouped by block size, the groups run concurrently) and
+ * one persistent stream-collide kernel over a shared list of tiles (32 x rows
+ * nodes of one z-plane) of every live realisation.  Steps are replayed from
+ * CUDA graphs of 1, 2 and 16 steps.
+ *
+ * A realisation is live while its state word is LBMD_RUNNING and it has taken
+ * fewer steps than the current cap (lbmd_ensemble_run; no cap before the first
+ * run).  The decision is taken on the device at the end of every step, so a
+ * realisation stops exactly at its translocation (or retraction, NaN, SHAKE
+ * failure) step or at the cap; its state then stays as it was.  Every step of
+ * a live realisation is the step lbmd_step would take for the same params.
+ *
+ * Same conventions as the single-box context: one caller workspace (256-byte
+ * aligned), the caller's stream, no device allocation, sticky CUDA errors.
+ */
+typedef struct lbmd_ensemble lbmd_ensemble;
+
+/*
+ * Workspace bytes for `count` realisations members[0 .. count-1].  Each member
+ * is validated as by lbmd_workspace_size and must further have
+ * n_beads >= 1 and 19 * nx*ny*nz < 2^31; all members must share storage and
+ * forcing (LBMD_EUNSUPPORTED otherwise).  count must be >= 1.
+ */
+int lbmd_ensemble_workspace_size(const lbmd_params *members, int32_t count, size_t *bytes);
+
+/*
+ * Create the ensemble: uploads every member's geometry, initial populations
+ * (f_eq(rho0, 0), or init_rho / init_u) and chain as lbmd_create does.  The
+ * host arrays in members are read during the call only.  Synchronises the
+ * stream.  Errors as lbmd_create.
+ */
+int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_workspace,
+                         size_t bytes, void *cuda_stream, lbmd_ensemble **out);
+
+/* Advance every live realisation by n_steps LB steps (asynchronous). */
+int lbmd_ensemble_step(lbmd_ensemble *ens, int64_t n_steps);
+
+/*
+ * Run until no realisation is live, with the step cap set to max_steps (total
+ * steps per realisation, counted from creation).  Realisations stopped only by
+ * an earlier, lower cap resume.  Every check_every steps (rounded up to a
+ * multiple of 16; <= 0 means 1024) the host counts the live realisations, stops
+ * when there are none and drops finished realisations from the tile list.
+ * Synchronises.  *steps_run (may be NULL) receives the LB steps enqueued by
+ * this call, i.e. those of its longest-running realisation rounded up to the
+ * check interval.
+ */
+int lbmd_ensemble_run(lbmd_ensemble *ens, int64_t max_steps, int64_t check_every,
+                      int64_t *steps_run);
+
+/*
+ * Per realisation (arrays of `count` entries; any pointer may be NULL): state
+ * word, first step with N_T = N (-1 if none), steps taken and N_T of the last
+ * step.  Synchronises.
+ */
+int lbmd_ensemble_results(lbmd_ensemble *ens, int32_t *state, int64_t *t_transloc,
+                          int64_t *steps, int32_t *n_trans);
+
+/* Number of realisations that take part in the next step.  Synchronises. */
+int lbmd_ensemble_live(lbmd_ensemble *ens, int32_t *n_live);
+
+/*
+ * Read-outs of realisation `member` (0-based), with the layout and
+ * dst_is_device meaning of lbmd_read_beads / lbmd_read_populations.  The
+ * populations are those after the realisation's last step.  Synchronise.
+ */
+int lbmd_ensemble_read_beads(lbmd_ensemble *ens, int32_t member, double *pos, double *vel,
+                             int dst_is_device);
+int lbmd_ensemble_read_populations(lbmd_ensemble *ens, int32_t member, float *f,
+                                   int dst_is_device);
+
+/*
+ * Launch shape of the ensemble stream-collide: tile height rows (4, 8 or 16),
+ * register budget for warps resident warps per SM (32: 64 registers, or 48: 40
+ * registers) and tiles taken per claim of the work counter (1 .. 64).
+ * Default (8, 48, 2).  The CUDA graphs are re-captured at the next step.
+ */
+int lbmd_ensemble_set_tuning(lbmd_ensemble *ens, int32_t rows, int32_t warps, int32_t claim);
+int lbmd_ensemble_get_tuning(lbmd_ensemble *ens, int32_t *rows, int32_t *warps, int32_t *claim);
+
+/*
+ * Autotuner: times the stream-collide alone, `trials` launches per shape, for
+ * every rows in {4, 8, 16} x warps in {32, 48} x claim in {1, 2, 4, 8}, on the
+ * live realisations' current populations, and keeps the fastest shape.  The
+ * trial launches write exactly what the next step's stream-collide writes
+ * (from the same input), so the simulation is unchanged.  *best_ms (may be
+ * NULL) receives the fastest average launch time.  Synchronises.
+ */
+int lbmd_ensemble_autotune(lbmd_ensemble *ens, int32_t trials, double *best_ms);
+
+/*
+ * Kernel timing for benchmarks: while enabled, lbmd_ensemble_step launches
+ * kernels directly (no graph) with CUDA events around each step and around
+ * its stream-collide.  lbmd_ensemble_kernel_times synchronises and returns the
+ * summed ms of the stream-collide launches, of the whole steps, and the number
+ * of timed steps since timing was enabled.  Any pointer may be NULL.
+ */
+int lbmd_ensemble_set_kernel_timing(lbmd_ensemble *ens, int enable);
+int lbmd_ensemble_kernel_times(lbmd_ensemble *ens, double *lb_ms, double *step_ms,
+                               int64_t *steps);
+
+/* Release the ensemble's host resources (not the caller's workspace). */
+int lbmd_ensemble_destroy(lbmd_ensemble *ens);
+
 /* Static description of a status code. */
 const char *lbmd_strerror(int status);
 

@@ -53,19 +53,13 @@ __device__ __forceinline__ void collide19(float h[kQ], const LbPhys &ph) {
   }
 }
 
-// Six 256-thread blocks per SM (40 registers): the occupancy that measured
-// fastest for this kernel; it is HBM-bound and needs the loads of many warps
-// in flight.
+// Stream and collide node (x, y, z) of one box: pull, Eq. 5 collision, store.
 template <int S, int FORCING, typename I>
-__global__ void __launch_bounds__(32 * kRowsPerBlock, 6)
-    k_stream_collide(LbGeom g, LbPhys ph, const typename Store<S>::T *__restrict__ src,
-                     typename Store<S>::T *__restrict__ dst, DevStatus *bump) {
+__device__ __forceinline__ void stream_collide_node(const LbGeom &g, const LbPhys &ph,
+                                                    const typename Store<S>::T *__restrict__ src,
+                                                    typename Store<S>::T *__restrict__ dst, int x,
+                                                    int y, int z) {
   using St = Store<S>;
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * kRowsPerBlock + threadIdx.y;
-  const int z = blockIdx.z;
-  if (bump != nullptr && x == 0 && y == 0 && z == 0) bump->step += 1;
-  if (x >= g.nx || y >= g.ny) return;
   const I self = ((I)z * g.ny + y) * g.nx + x;
   float h[kQ];
   if (tile_is_near(g, x, y, z)) {
@@ -78,6 +72,56 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock, 6)
   const I Vp = (I)g.Vp;
 #pragma unroll
   for (int p = 0; p < kQ; ++p) St::store(dst + (I)p * Vp + self, h[p]);
+}
+
+// Six 256-thread blocks per SM (40 registers): the occupancy that measured
+// fastest for this kernel; it is HBM-bound and needs the loads of many warps
+// in flight.
+template <int S, int FORCING, typename I>
+__global__ void __launch_bounds__(32 * kRowsPerBlock, 6)
+    k_stream_collide(LbGeom g, LbPhys ph, const typename Store<S>::T *__restrict__ src,
+                     typename Store<S>::T *__restrict__ dst, DevStatus *bump) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kRowsPerBlock + threadIdx.y;
+  const int z = blockIdx.z;
+  if (bump != nullptr && x == 0 && y == 0 && z == 0) bump->step += 1;
+  if (x >= g.nx || y >= g.ny) return;
+  stream_collide_node<S, FORCING, I>(g, ph, src, dst, x, y, z);
+}
+
+// Ensemble stream-collide: a persistent grid over the tiles of every live
+// realisation.  A block takes `claim` consecutive tiles at a time from a
+// global counter, so blocks that become resident late (after the MD blocks of
+// the same step) simply take fewer tiles.  WARPS is the occupancy the
+// register budget is sized for: 48 warps per SM (40 registers, a little
+// spilling) or 32 (64 registers, none); population offsets are 32-bit.
+template <int S, int FORCING, int ROWS, int WARPS>
+__global__ void __launch_bounds__(32 * ROWS, WARPS / ROWS)
+    k_ens_stream_collide(const EnsMember *__restrict__ mem, const EnsTile *__restrict__ tiles,
+                         const int *__restrict__ n_tiles, int *__restrict__ counter,
+                         const int *__restrict__ live, int cur, int claim) {
+  using T = typename Store<S>::T;
+  __shared__ int s_first;
+  const int n = *n_tiles;
+  const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+  for (;;) {
+    if (leader) s_first = atomicAdd(counter, claim);
+    __syncthreads();
+    const int first = s_first;
+    __syncthreads();
+    if (first >= n) return;
+    const int last = min(first + claim, n);
+    for (int t = first; t < last; ++t) {
+      const EnsTile w = tiles[t];
+      if (!live[w.m]) continue;
+      const EnsMember &M = mem[w.m];
+      const LbGeom g = M.a.geo;
+      const int x = w.bx * 32 + threadIdx.x, y = w.by * ROWS + threadIdx.y;
+      if (x < g.nx && y < g.ny)
+        stream_collide_node<S, FORCING, int>(g, M.ph, (const T *)M.pop[cur], (T *)M.pop[cur ^ 1],
+                                             x, y, w.z);
+    }
+  }
 }
 
 template <int S, typename I>
@@ -110,6 +154,65 @@ cudaError_t launch_lb_stream_collide(int storage, const LbGeom &g, const LbPhys 
     case LBMD_STORE_BF16: return lb_launch<LBMD_STORE_BF16>(g, ph, src, dst, bump, s);
   }
   return cudaErrorInvalidValue;
+}
+
+template <int S, int FORCING, int ROWS, int WARPS>
+static cudaError_t ens_lb_launch(int claim, int grid, const EnsMember *mem, const EnsTile *tiles,
+                                 const int *n_tiles, int *counter, const int *live, int cur,
+                                 cudaStream_t s) {
+  k_ens_stream_collide<S, FORCING, ROWS, WARPS><<<grid, dim3(32, ROWS), 0, s>>>(
+      mem, tiles, n_tiles, counter, live, cur, claim);
+  return cudaGetLastError();
+}
+
+template <int S, int FORCING, int ROWS, int WARPS>
+static int ens_lb_occupancy() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_stream_collide<S, FORCING, ROWS, WARPS>,
+                                                    32 * ROWS, 0) != cudaSuccess)
+    return 0;
+  return n;
+}
+
+// Dispatch on (storage, forcing, rows, warps per SM) to one instantiation.
+struct EnsLbFns {
+  cudaError_t (*launch)(int, int, const EnsMember *, const EnsTile *, const int *, int *,
+                        const int *, int, cudaStream_t);
+  int (*occupancy)();
+};
+template <int S, int F, int R>
+static EnsLbFns ens_fns_warps(int warps) {
+  if (warps == 32) return {&ens_lb_launch<S, F, R, 32>, &ens_lb_occupancy<S, F, R, 32>};
+  return {&ens_lb_launch<S, F, R, 48>, &ens_lb_occupancy<S, F, R, 48>};
+}
+template <int S, int F>
+static EnsLbFns ens_fns_rows(int rows, int warps) {
+  if (rows == 4) return ens_fns_warps<S, F, 4>(warps);
+  if (rows == 16) return ens_fns_warps<S, F, 16>(warps);
+  return ens_fns_warps<S, F, 8>(warps);
+}
+template <int S>
+static EnsLbFns ens_fns_store(int forcing, int rows, int warps) {
+  if (forcing == LBMD_FORCING_GUO) return ens_fns_rows<S, LBMD_FORCING_GUO>(rows, warps);
+  return ens_fns_rows<S, LBMD_FORCING_PAPER>(rows, warps);
+}
+static EnsLbFns ens_fns(int storage, int forcing, int rows, int warps) {
+  if (storage == LBMD_STORE_F16) return ens_fns_store<LBMD_STORE_F16>(forcing, rows, warps);
+  if (storage == LBMD_STORE_BF16) return ens_fns_store<LBMD_STORE_BF16>(forcing, rows, warps);
+  return ens_fns_store<LBMD_STORE_F32>(forcing, rows, warps);
+}
+
+cudaError_t launch_ens_stream_collide(int storage, int forcing, int rows, int warps, int claim,
+                                      int grid, const EnsMember *mem, const EnsTile *tiles,
+                                      const int *n_tiles, int *counter, const int *live, int cur,
+                                      cudaStream_t s) {
+  if (storage < LBMD_STORE_F32 || storage > LBMD_STORE_BF16) return cudaErrorInvalidValue;
+  return ens_fns(storage, forcing, rows, warps).launch(claim, grid, mem, tiles, n_tiles, counter,
+                                                       live, cur, s);
+}
+
+int ens_lb_blocks_per_sm(int storage, int forcing, int rows, int warps) {
+  return ens_fns(storage, forcing, rows, warps).occupancy();
 }
 
 // ---------------------------------------------------------------------------

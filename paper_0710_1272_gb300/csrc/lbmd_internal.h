@@ -20,6 +20,7 @@ struct DevStatus {
   int newton_iters;      // Newton iterations of the last LB step (all substeps)
   int nl_builds;         // neighbour-list builds so far (0: none yet)
   int nl_ok;             // 1 if the current lists hold every pair (no overflow)
+  int out_buf;           // ensemble: population buffer (0/1) written by the last step
 };
 
 // Neighbour-list capacities per bead: bead partners and solid nodes within
@@ -72,10 +73,25 @@ struct ChainArgs {
   DevStatus *status;
 };
 
+// One realisation of an ensemble as every ensemble kernel sees it: its box,
+// its chain and its two population buffers.  An array of these lives in
+// device memory; kernels index it by realisation.
+struct EnsMember {
+  ChainArgs a;      // chain, geometry (a.geo) and bead buffers; a.f unused
+  LbPhys ph;
+  void *pop[2];     // post-collision populations, swapped every step
+};
+
+// Work item of the ensemble stream-collide: one block-sized tile (32 x rows
+// nodes of one z-plane) of realisation m.
+struct EnsTile {
+  int m, bx, by, z;
+};
+
 size_t md_smem_bytes(int N);
 int md_threads(int N);
-// Opt the MD kernel into the dynamic shared memory a chain of N beads needs.
-cudaError_t md_prepare(int N);
+// Opt the MD kernels into the dynamic shared memory of the longest chain.
+cudaError_t md_prepare();
 
 // Launchers (each returns the launch error, if any).
 cudaError_t launch_lb_stream_collide(int storage, const LbGeom &g, const LbPhys &ph,
@@ -95,6 +111,32 @@ cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s);
 cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, const float *sp_w,
                           const float4 *J, int N, int nw, void *dst, DevStatus *bump,
                           cudaStream_t s);
+// Ensemble launchers.  `live` points at the flags of the current step (one int
+// per realisation); realisations whose flag is 0 are skipped by every kernel.
+// Stream-collide: persistent grid of `grid` blocks of 32 x rows threads (rows
+// 4, 8 or 16; registers sized for `warps` = 32 or 48 resident warps per SM)
+// taking `claim` tiles at a time from `counter` (reset by the ensemble
+// gather).  Every realisation must have 19 Vp < 2^31 (32-bit offsets).
+cudaError_t launch_ens_stream_collide(int storage, int forcing, int rows, int warps, int claim,
+                                      int grid, const EnsMember *mem, const EnsTile *tiles,
+                                      const int *n_tiles, int *counter, const int *live, int cur,
+                                      cudaStream_t s);
+// Blocks of that kernel that fit on one SM.
+int ens_lb_blocks_per_sm(int storage, int forcing, int rows, int warps);
+// Gather for every (realisation, bead) of `beads` (padded entries have m < 0).
+cudaError_t launch_ens_gather(int storage, const EnsMember *mem, const int2 *beads, int nb,
+                              const int *live, int cur, int *counter, cudaStream_t s);
+// MD cycle of the `count` chains listed in `chains`, one block of `threads`
+// threads each, with dynamic shared memory for `max_n` beads.
+cudaError_t launch_ens_md_cycle(const EnsMember *mem, const int *chains, int count, int threads,
+                                int max_n, const int *live, int priority, cudaStream_t s);
+// Spread of the bead impulses into pop[1 - cur]; bumps each live realisation's
+// step count and writes its flag for the next step into `live_next`
+// (still running and step < *max_steps).
+cudaError_t launch_ens_spread(int storage, const EnsMember *mem, const int2 *beads, int nb,
+                              const int *live, int *live_next, int cur,
+                              const long long *max_steps, cudaStream_t s);
+
 cudaError_t launch_read_beads(const float4 *pos, const float4 *pos_lo, const float4 *vel, int N,
                               int ox, int oy, int oz, double *dpos, double *dvel, cudaStream_t s);
 cudaError_t launch_read_bead_aux(const float4 *ui, const float4 *J, int N, double *dui,

@@ -411,8 +411,9 @@ __device__ F3 wall_stencil_forces(const ChainArgs &a, float4 rh, float4 rl) {
   return F;
 }
 
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_md_cycle(ChainArgs a) {
+// (2) the M MD substeps of one chain, one thread per bead, and (5) the
+// bookkeeping; `a` may live in parameter or shared memory.
+__device__ __forceinline__ void md_cycle_body(const ChainArgs &a) {
   extern __shared__ float4 smem4[];
   const int N = a.N;
   const int i = threadIdx.x;  // bead of this thread
@@ -625,12 +626,34 @@ __global__ void __launch_bounds__(BLOCK) k_md_cycle(ChainArgs a) {
   }
 }
 
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_md_cycle(ChainArgs a) {
+  md_cycle_body(a);
+}
+
+// Ensemble variant: block b runs chain chains[b] if its realisation is live.
+// The chain's arguments are copied to shared memory once.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_ens_md_cycle(const EnsMember *__restrict__ mem, const int *__restrict__ chains,
+                   const int *__restrict__ live) {
+  __shared__ ChainArgs s_a;
+  const int m = chains[blockIdx.x];
+  if (!live[m]) return;  // the whole block leaves together
+  static_assert(sizeof(ChainArgs) % sizeof(int) == 0, "ChainArgs copied as ints");
+  const int *src = reinterpret_cast<const int *>(&mem[m].a);
+  int *dst = reinterpret_cast<int *>(&s_a);
+  for (int k = threadIdx.x; k < (int)(sizeof(ChainArgs) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
+  md_cycle_body(s_a);
+}
+
 // Stage (1) for (bead, corner) pair e = 8 i + k handled by one thread; the
 // eight lanes of a bead are consecutive, so the weight normalisation and the
 // sum over corners are lane shuffles.  Writes the transfer weights for the
 // spread and returns the bead's interpolated u (on every lane of the bead).
 template <int S>
-__device__ F3 gather_pair(const ChainArgs &a, int e, bool valid) {
+__device__ F3 gather_pair(const ChainArgs &a, const void *f, int e, bool valid) {
   using T = typename Store<S>::T;
   const LbGeom &g = a.geo;
   const int i = e >> 3, k = e & 7;
@@ -676,9 +699,9 @@ __device__ F3 gather_pair(const ChainArgs &a, int e, bool valid) {
       const int y = yz % g.ny, z = yz / g.ny;
       float h[kQ];
       if (tile_is_near(g, x, y, z))
-        pull19<S, true>(g, (const T *)a.f, x, y, z, h);
+        pull19<S, true>(g, (const T *)f, x, y, z, h);
       else
-        pull19<S, false>(g, (const T *)a.f, x, y, z, h);
+        pull19<S, false>(g, (const T *)f, x, y, z, h);
       float drho, jx, jy, jz;
       moments19(h, drho, jx, jy, jz);
       if (a.forcing == LBMD_FORCING_GUO) {
@@ -703,15 +726,36 @@ template <int S>
 __global__ void __launch_bounds__(256) k_gather(ChainArgs a) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = e < 8 * a.N;
-  const F3 u = gather_pair<S>(a, e, valid);
+  const F3 u = gather_pair<S>(a, a.f, e, valid);
   if (valid && (e & 7) == 0) a.ui[e >> 3] = f4(u);
 }
 
-cudaError_t md_prepare(int N) {
-  const int smem = (int)md_smem_bytes(N);
-  cudaError_t e = cudaFuncSetAttribute(k_md_cycle<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_md_cycle<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+// Ensemble gather: thread e serves corner e & 7 of padded bead slot e >> 3,
+// beads[slot] = (realisation, bead) or m < 0 for padding.  Every realisation's
+// slots start at a multiple of four, so a warp never mixes realisations.
+// Thread 0 also resets the work counter of this step's stream-collide.
+template <int S>
+__global__ void __launch_bounds__(256)
+    k_ens_gather(const EnsMember *__restrict__ mem, const int2 *__restrict__ beads, int nb,
+                 const int *__restrict__ live, int cur, int *counter) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e == 0) *counter = 0;
+  const int slot = e >> 3;
+  int2 mi = make_int2(-1, 0);
+  if (slot < nb) mi = beads[slot];
+  const bool valid = mi.x >= 0 && live[mi.x];
+  const EnsMember &M = mem[valid ? mi.x : 0];
+  const F3 u = gather_pair<S>(M.a, valid ? M.pop[cur] : nullptr, 8 * mi.y + (e & 7), valid);
+  if (valid && (e & 7) == 0) M.a.ui[mi.y] = f4(u);
+}
+
+cudaError_t md_prepare() {
+  const int smem = (int)md_smem_bytes(LBMD_MAX_BEADS);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_md_cycle<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_md_cycle<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_ens_md_cycle<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_ens_md_cycle<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 cudaError_t launch_gather(int storage, const ChainArgs &a, cudaStream_t s) {
@@ -808,6 +852,109 @@ cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, cons
       break;
     default:
       return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Ensemble spread: same lane layout as k_ens_gather, so a warp holds lanes of
+// one realisation only and matching on the node index suffices.  The first
+// lane of every realisation bumps its step count (if live) and decides
+// whether it takes part in the next step.
+template <int S>
+__global__ void __launch_bounds__(256)
+    k_ens_spread(const EnsMember *__restrict__ mem, const int2 *__restrict__ beads, int nb,
+                 const int *__restrict__ live, int *__restrict__ live_next, int cur,
+                 const long long *__restrict__ max_steps) {
+  using St = Store<S>;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int slot = e >> 3, k = e & 7;
+  const int lane = threadIdx.x & 31;
+  int2 mi = make_int2(-1, 0);
+  if (slot < nb) mi = beads[slot];
+  const bool valid = mi.x >= 0 && live[mi.x];
+  int node = -1;
+  F3 F{0.f, 0.f, 0.f};
+  if (valid) {
+    const ChainArgs &a = mem[mi.x].a;
+    const int ee = 8 * mi.y + k;
+    node = a.sp_node[ee];
+    if (node >= 0) {
+      const float w = a.sp_w[ee];
+      const float4 j = a.J[mi.y];
+      F = F3{-w * j.x, -w * j.y, -w * j.z};
+    }
+  }
+  const unsigned peers = __match_any_sync(0xffffffffu, node);
+  F3 sum{0.f, 0.f, 0.f};
+#pragma unroll 4
+  for (int l = 0; l < 32; ++l) {
+    const float vx = __shfl_sync(0xffffffffu, F.x, l);
+    const float vy = __shfl_sync(0xffffffffu, F.y, l);
+    const float vz = __shfl_sync(0xffffffffu, F.z, l);
+    if ((peers >> l) & 1u) sum = sum + F3{vx, vy, vz};
+  }
+  const int leader = __ffs(peers) - 1;
+  if (node >= 0 && lane == leader) {
+    const EnsMember &M = mem[mi.x];
+    typename St::T *dst = (typename St::T *)M.pop[cur ^ 1];
+    const size_t Vp = (size_t)M.a.geo.Vp;
+#pragma unroll
+    for (int p = 1; p < kQ; ++p) {
+      const float cf = cx(p) * sum.x + cy(p) * sum.y + cz(p) * sum.z;
+      St::add(dst + (size_t)p * Vp + node, 3.0f * wq(p) * cf);
+    }
+  }
+  if (mi.x >= 0 && mi.y == 0 && k == 0) {
+    int next = 0;
+    if (valid) {
+      DevStatus *st = mem[mi.x].a.status;
+      const long long s = st->step + 1;
+      st->step = s;
+      st->out_buf = cur ^ 1;
+      next = st->state == LBMD_RUNNING && s < *max_steps;
+    }
+    live_next[mi.x] = next;
+  }
+}
+
+cudaError_t launch_ens_gather(int storage, const EnsMember *mem, const int2 *beads, int nb,
+                              const int *live, int cur, int *counter, cudaStream_t s) {
+  const int blocks = nb > 0 ? (8 * nb + 255) / 256 : 1;
+  switch (storage) {
+    case LBMD_STORE_F32: k_ens_gather<LBMD_STORE_F32><<<blocks, 256, 0, s>>>(mem, beads, nb, live, cur, counter); break;
+    case LBMD_STORE_F16: k_ens_gather<LBMD_STORE_F16><<<blocks, 256, 0, s>>>(mem, beads, nb, live, cur, counter); break;
+    case LBMD_STORE_BF16: k_ens_gather<LBMD_STORE_BF16><<<blocks, 256, 0, s>>>(mem, beads, nb, live, cur, counter); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ens_md_cycle(const EnsMember *mem, const int *chains, int count, int threads,
+                                int max_n, const int *live, int priority, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)count);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = md_smem_bytes(max_n);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = priority;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (threads <= 512) return cudaLaunchKernelEx(&cfg, k_ens_md_cycle<512>, mem, chains, live);
+  return cudaLaunchKernelEx(&cfg, k_ens_md_cycle<1024>, mem, chains, live);
+}
+
+cudaError_t launch_ens_spread(int storage, const EnsMember *mem, const int2 *beads, int nb,
+                              const int *live, int *live_next, int cur,
+                              const long long *max_steps, cudaStream_t s) {
+  const int blocks = nb > 0 ? (8 * nb + 255) / 256 : 1;
+  switch (storage) {
+    case LBMD_STORE_F32: k_ens_spread<LBMD_STORE_F32><<<blocks, 256, 0, s>>>(mem, beads, nb, live, live_next, cur, max_steps); break;
+    case LBMD_STORE_F16: k_ens_spread<LBMD_STORE_F16><<<blocks, 256, 0, s>>>(mem, beads, nb, live, live_next, cur, max_steps); break;
+    case LBMD_STORE_BF16: k_ens_spread<LBMD_STORE_BF16><<<blocks, 256, 0, s>>>(mem, beads, nb, live, live_next, cur, max_steps); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

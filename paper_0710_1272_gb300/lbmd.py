@@ -58,6 +58,14 @@ class lbmd_params(C.Structure):
 
 _lib = None
 
+ENSEMBLE_FUNCTIONS = (
+    "lbmd_ensemble_workspace_size", "lbmd_ensemble_create", "lbmd_ensemble_step", "lbmd_ensemble_run",
+    "lbmd_ensemble_results", "lbmd_ensemble_live", "lbmd_ensemble_read_beads",
+    "lbmd_ensemble_read_populations", "lbmd_ensemble_set_tuning", "lbmd_ensemble_get_tuning",
+    "lbmd_ensemble_autotune", "lbmd_ensemble_set_kernel_timing", "lbmd_ensemble_kernel_times",
+    "lbmd_ensemble_destroy",
+)
+
 
 class LbmdError(RuntimeError):
     def __init__(self, code: int, where: str):
@@ -96,13 +104,29 @@ def load(build_if_missing: bool = True):
                                     C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.lbmd_lb_step_noalloc.argtypes = [C.POINTER(lbmd_params), P, P, P]
     L.lbmd_destroy.argtypes = [P]
+    PI32, PI64, PD = C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_double)
+    L.lbmd_ensemble_workspace_size.argtypes = [C.POINTER(lbmd_params), C.c_int32, C.POINTER(C.c_size_t)]
+    L.lbmd_ensemble_create.argtypes = [C.POINTER(lbmd_params), C.c_int32, P, C.c_size_t, P, C.POINTER(P)]
+    L.lbmd_ensemble_step.argtypes = [P, C.c_int64]
+    L.lbmd_ensemble_run.argtypes = [P, C.c_int64, C.c_int64, PI64]
+    L.lbmd_ensemble_results.argtypes = [P, P, P, P, P]
+    L.lbmd_ensemble_live.argtypes = [P, PI32]
+    L.lbmd_ensemble_read_beads.argtypes = [P, C.c_int32, P, P, C.c_int]
+    L.lbmd_ensemble_read_populations.argtypes = [P, C.c_int32, P, C.c_int]
+    L.lbmd_ensemble_set_tuning.argtypes = [P, C.c_int32, C.c_int32, C.c_int32]
+    L.lbmd_ensemble_get_tuning.argtypes = [P, PI32, PI32, PI32]
+    L.lbmd_ensemble_autotune.argtypes = [P, C.c_int32, PD]
+    L.lbmd_ensemble_set_kernel_timing.argtypes = [P, C.c_int]
+    L.lbmd_ensemble_kernel_times.argtypes = [P, PD, PD, PI64]
+    L.lbmd_ensemble_destroy.argtypes = [P]
     L.lbmd_strerror.argtypes = [C.c_int]
     L.lbmd_strerror.restype = C.c_char_p
     L.lbmd_last_message.restype = C.c_char_p
     for name in ("lbmd_workspace_size", "lbmd_create", "lbmd_step", "lbmd_read_fields",
                  "lbmd_read_populations", "lbmd_read_beads", "lbmd_read_bead_aux", "lbmd_status",
                  "lbmd_set_kernel_timing", "lbmd_lb_kernel_time", "lbmd_destroy", "lbmd_version",
-                 "lbmd_solver_stats", "lbmd_kernel_times", "lbmd_lb_step_noalloc"):
+                 "lbmd_solver_stats", "lbmd_kernel_times", "lbmd_lb_step_noalloc",
+                 *ENSEMBLE_FUNCTIONS):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -246,6 +270,92 @@ def lbmd_version() -> int:
     return load().lbmd_version()
 
 
+# -- ensemble entry points ----------------------------------------------------
+def lbmd_ensemble_workspace_size(members) -> int:
+    n = C.c_size_t()
+    _check(load().lbmd_ensemble_workspace_size(members, len(members), C.byref(n)),
+           "lbmd_ensemble_workspace_size")
+    return n.value
+
+
+def lbmd_ensemble_create(members, workspace_ptr: int, nbytes: int, stream_ptr: int):
+    h = C.c_void_p()
+    _check(load().lbmd_ensemble_create(members, len(members), C.c_void_p(workspace_ptr), nbytes,
+                                       C.c_void_p(stream_ptr), C.byref(h)), "lbmd_ensemble_create")
+    return h
+
+
+def lbmd_ensemble_step(ens, n: int) -> None:
+    _check(load().lbmd_ensemble_step(ens, int(n)), "lbmd_ensemble_step")
+
+
+def lbmd_ensemble_run(ens, max_steps: int, check_every: int = 1024) -> int:
+    n = C.c_int64()
+    _check(load().lbmd_ensemble_run(ens, int(max_steps), int(check_every), C.byref(n)),
+           "lbmd_ensemble_run")
+    return n.value
+
+
+def lbmd_ensemble_results(ens, count: int) -> dict:
+    state = np.empty(count, np.int32)
+    tt = np.empty(count, np.int64)
+    steps = np.empty(count, np.int64)
+    nt = np.empty(count, np.int32)
+    _check(load().lbmd_ensemble_results(ens, state.ctypes.data, tt.ctypes.data, steps.ctypes.data,
+                                        nt.ctypes.data), "lbmd_ensemble_results")
+    return dict(state=state, t_transloc=tt, steps=steps, n_trans=nt)
+
+
+def lbmd_ensemble_live(ens) -> int:
+    n = C.c_int32()
+    _check(load().lbmd_ensemble_live(ens, C.byref(n)), "lbmd_ensemble_live")
+    return n.value
+
+
+def lbmd_ensemble_read_beads(ens, member: int, pos_ptr, vel_ptr, dst_is_device: int) -> None:
+    _check(load().lbmd_ensemble_read_beads(ens, int(member), pos_ptr, vel_ptr, dst_is_device),
+           "lbmd_ensemble_read_beads")
+
+
+def lbmd_ensemble_read_populations(ens, member: int, f_ptr, dst_is_device: int) -> None:
+    _check(load().lbmd_ensemble_read_populations(ens, int(member), f_ptr, dst_is_device),
+           "lbmd_ensemble_read_populations")
+
+
+def lbmd_ensemble_set_tuning(ens, rows: int, warps: int, claim: int) -> None:
+    _check(load().lbmd_ensemble_set_tuning(ens, int(rows), int(warps), int(claim)),
+           "lbmd_ensemble_set_tuning")
+
+
+def lbmd_ensemble_get_tuning(ens) -> dict:
+    r, w, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().lbmd_ensemble_get_tuning(ens, C.byref(r), C.byref(w), C.byref(c)),
+           "lbmd_ensemble_get_tuning")
+    return dict(rows=r.value, warps=w.value, claim=c.value)
+
+
+def lbmd_ensemble_autotune(ens, trials: int = 3) -> float:
+    ms = C.c_double()
+    _check(load().lbmd_ensemble_autotune(ens, int(trials), C.byref(ms)), "lbmd_ensemble_autotune")
+    return ms.value
+
+
+def lbmd_ensemble_set_kernel_timing(ens, enable: bool) -> None:
+    _check(load().lbmd_ensemble_set_kernel_timing(ens, int(bool(enable))),
+           "lbmd_ensemble_set_kernel_timing")
+
+
+def lbmd_ensemble_kernel_times(ens) -> dict:
+    lb, st, n = C.c_double(), C.c_double(), C.c_int64()
+    _check(load().lbmd_ensemble_kernel_times(ens, C.byref(lb), C.byref(st), C.byref(n)),
+           "lbmd_ensemble_kernel_times")
+    return dict(lb_ms=lb.value, step_ms=st.value, steps=n.value)
+
+
+def lbmd_ensemble_destroy(ens) -> None:
+    _check(load().lbmd_ensemble_destroy(ens), "lbmd_ensemble_destroy")
+
+
 # -- convenience wrapper owning a torch workspace ---------------------------
 class Simulation:
     """One box with (optionally) one chain, stepped on the GPU.
@@ -339,3 +449,87 @@ class Simulation:
 
     def kernel_times(self) -> dict:
         return lbmd_kernel_times(self.ctx)
+
+
+class Ensemble:
+    """Many independent realisations (each a params dict with its own box,
+    chain and seed; same storage and forcing) stepped together on the GPU.
+
+    ``init_pos[k]`` is the (N_k, 3) start of chain k.  The device workspace is
+    a torch uint8 tensor owned by this object."""
+
+    def __init__(self, members, init_pos, device: str = "cuda", stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        if len(members) != len(init_pos):
+            raise ValueError("one init_pos per member")
+        self.p = [full_params(m) for m in members]
+        self.count = len(self.p)
+        self.device = torch.device(device)
+        arr = (lbmd_params * self.count)()
+        keep = []
+        for k, (m, pos) in enumerate(zip(self.p, init_pos)):
+            cp, kk = make_params(m, init_pos=pos)
+            arr[k] = cp
+            keep.append(kk)
+        nbytes = lbmd_ensemble_workspace_size(arr)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            self.ens = lbmd_ensemble_create(arr, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        del keep
+        self.workspace_bytes = nbytes
+        self.N = [int(m["n_beads"]) for m in self.p]
+        self.shapes = [(int(m["nz"]), int(m["ny"]), int(m["nx"])) for m in self.p]
+
+    def close(self) -> None:
+        if getattr(self, "ens", None):
+            lbmd_ensemble_destroy(self.ens)
+            self.ens = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1) -> None:
+        lbmd_ensemble_step(self.ens, n)
+
+    def run(self, max_steps: int, check_every: int = 1024) -> int:
+        return lbmd_ensemble_run(self.ens, max_steps, check_every)
+
+    def results(self) -> dict:
+        return lbmd_ensemble_results(self.ens, self.count)
+
+    def live(self) -> int:
+        return lbmd_ensemble_live(self.ens)
+
+    def beads(self, member: int):
+        N = self.N[member]
+        pos = np.empty((N, 3))
+        vel = np.empty((N, 3))
+        lbmd_ensemble_read_beads(self.ens, member, pos.ctypes.data, vel.ctypes.data, 0)
+        return pos, vel
+
+    def populations(self, member: int) -> np.ndarray:
+        f = np.empty((19,) + self.shapes[member], dtype=np.float32)
+        lbmd_ensemble_read_populations(self.ens, member, f.ctypes.data, 0)
+        return f
+
+    def set_tuning(self, rows: int, warps: int, claim: int) -> None:
+        lbmd_ensemble_set_tuning(self.ens, rows, warps, claim)
+
+    def tuning(self) -> dict:
+        return lbmd_ensemble_get_tuning(self.ens)
+
+    def autotune(self, trials: int = 3) -> float:
+        return lbmd_ensemble_autotune(self.ens, trials)
+
+    def set_kernel_timing(self, enable: bool) -> None:
+        lbmd_ensemble_set_kernel_timing(self.ens, enable)
+
+    def kernel_times(self) -> dict:
+        return lbmd_ensemble_kernel_times(self.ens)

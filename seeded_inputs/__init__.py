@@ -66,6 +66,32 @@ def ensemble_box(n_beads: int) -> tuple[int, int, int]:
     return max(r16(4 * a), 32), max(r16(2 * a), 16), max(r16(2 * a), 16)
 
 
+def ragged_member(n_beads: int, pore_d: int, seed: int, **overrides) -> dict:
+    """One realisation of the ragged ensemble: box from ensemble_box(N), wall
+    at x = N_x / 2 with a centred d x d pore, paper bead parameters."""
+    nx, ny, nz = ensemble_box(n_beads)
+    p = dict(BASE)
+    p.update(nx=nx, ny=ny, nz=nz, wall_x=nx // 2, pore_d=pore_d, n_beads=n_beads, seed=seed)
+    p.update(overrides)
+    return p
+
+
+def ragged_ensemble(count: int, seed: int = 0, lengths=(20, 50, 100, 200, 400), pores=(3, 5),
+                    **overrides):
+    """`count` realisations with N drawn uniformly from `lengths` and d from
+    `pores` (seeded), realisation k seeded with seed * 1_000_003 + k, each with
+    its own self-avoiding start.  Returns (list of params, list of (N, 3))."""
+    rng = np.random.default_rng(seed)
+    members, starts = [], []
+    for k in range(count):
+        n = int(rng.choice(lengths))
+        d = int(rng.choice(pores))
+        p = ragged_member(n, d, seed * 1_000_003 + k, **overrides)
+        members.append(p)
+        starts.append(saw_chain(p, p["seed"]))
+    return members, starts
+
+
 def taylor_green_field(nx: int, ny: int, nz: int, amp: float) -> np.ndarray:
     """u = A (sin kx cos ky, -cos kx sin ky, 0), k = 2 pi / L; shape (3, nz, ny, nx)."""
     x = np.arange(nx)[None, None, :]

@@ -93,3 +93,46 @@ def test_null_context_is_an_error():
     assert L.lbmd_step(None, 1) == lb.lbmd.LBMD_EINVAL
     assert L.lbmd_destroy(None) == 0
     assert L.lbmd_strerror(-3) == b"CUDA error"
+
+
+def _ens_ws(members, starts):
+    arr = (lb.lbmd.lbmd_params * len(members))()
+    keep = []
+    for k, (p, pos) in enumerate(zip(members, starts)):
+        cp, kk = lb.make_params(p, init_pos=pos)
+        arr[k] = cp
+        keep.append(kk)
+    return lb.lbmd.lbmd_ensemble_workspace_size(arr)
+
+
+def test_ensemble_workspace_holds_every_member():
+    members, starts = si.ragged_ensemble(6, seed=3)
+    n = _ens_ws(members, starts)
+    singles = sum(_ws(p, init_pos=pos) for p, pos in zip(members, starts))
+    pops = sum(2 * 19 * p["nx"] * p["ny"] * p["nz"] * 4 for p in members)
+    # every member's buffers, but one shared read-out staging area
+    assert pops < n < singles + 8 * 2 ** 20
+
+
+@pytest.mark.parametrize("change,code", [
+    (lambda m: m[1].update(storage="f16"), lb.lbmd.LBMD_EUNSUPPORTED),
+    (lambda m: m[2].update(forcing="guo"), lb.lbmd.LBMD_EUNSUPPORTED),
+    (lambda m: m[0].update(tau=0.4), lb.lbmd.LBMD_EINVAL),
+])
+def test_ensemble_rejects_mixed_or_bad_members(change, code):
+    members, starts = si.ragged_ensemble(3, seed=4)
+    change(members)
+    with pytest.raises(lb.LbmdError) as e:
+        _ens_ws(members, starts)
+    assert e.value.code == code
+
+
+def test_ensemble_rejects_empty_and_beadless():
+    L = lb.load()
+    n = ctypes.c_size_t()
+    assert L.lbmd_ensemble_workspace_size(None, 0, ctypes.byref(n)) == lb.lbmd.LBMD_EINVAL
+    p = dict(si.periodic_solvent(16))
+    cp, keep = lb.make_params(p)
+    arr = (lb.lbmd.lbmd_params * 1)(cp)
+    assert L.lbmd_ensemble_workspace_size(arr, 1, ctypes.byref(n)) == lb.lbmd.LBMD_EINVAL
+    assert L.lbmd_ensemble_workspace_size(arr, 0, ctypes.byref(n)) == lb.lbmd.LBMD_EINVAL

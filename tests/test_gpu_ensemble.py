@@ -1,0 +1,223 @@
+"""GPU parity of the ensemble path (many realisations in one set of launches):
+every realisation must take exactly the steps the FP64 oracle takes for its
+own parameters, within the tolerances of the single-box parity tests
+(populations 1e-5 relative after one step, beads 1e-4 over 100 steps), and
+must stop at its own translocation step or at the step cap.
+
+The members are ragged on purpose: different boxes (x extents that are not a
+multiple of the 32-node tile, odd y and z), chain lengths in different MD
+block-size groups, pore sizes, seeds and bead parameters.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+GPU_ONLY = ("storage", "init_tg_amp")
+PAPER_EPS = 2e-3
+
+
+def _lb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_0710_1272_gb300 as lb
+    return lb
+
+
+def rel_err(fg, fo):
+    m = fo != 0
+    assert np.all(fg[~m] == 0)
+    return float(np.max(np.abs(fg[m].astype(np.float64) - fo[m]) / np.abs(fo[m])))
+
+
+def ragged_members(storage="f32", eps=PAPER_EPS):
+    specs = [
+        dict(nx=32, ny=16, nz=16, wall_x=16, pore_d=3, n_beads=20, seed=11),
+        dict(nx=48, ny=20, nz=13, wall_x=24, pore_d=5, n_beads=37, seed=12, gamma=0.2),
+        dict(nx=40, ny=17, nz=17, wall_x=20, pore_d=3, n_beads=5, seed=13, tau=0.8),
+        dict(nx=64, ny=24, nz=24, wall_x=32, pore_d=5, n_beads=70, seed=14, f_drive=0.05),
+        dict(nx=36, ny=16, nz=16, wall_x=18, pore_d=3, n_beads=1, seed=15),
+    ]
+    members, starts = [], []
+    for sp in specs:
+        p = dict(si.BASE)
+        p.update(sp)
+        p["lj_eps"] = eps
+        starts.append(si.saw_chain(p, p["seed"]))
+        p["storage"] = storage
+        members.append(p)
+    return members, starts
+
+
+def oracle_of(p, pos):
+    return oracle.OracleSim({k: v for k, v in p.items() if k not in GPU_ONLY}, init_pos=pos)
+
+
+def advance_like_member(sim, n, running=0):
+    """Step a reference (oracle or single-box context) n steps, one at a time,
+    stopping as an ensemble member does once its state leaves RUNNING."""
+    for _ in range(n):
+        if sim.status()["state"] != running:
+            break
+        sim.step(1)
+
+
+def test_ensemble_members_match_oracle_one_step():
+    lb = _lb()
+    members, starts = ragged_members()
+    ens = lb.Ensemble(members, starts)
+    ens.step(1)
+    for k, (p, pos) in enumerate(zip(members, starts)):
+        orc = oracle_of(p, pos)
+        orc.step(1)
+        assert rel_err(ens.populations(k), orc.populations()) < 1e-5, k
+        assert np.abs(ens.beads(k)[0] - orc.beads()[0]).max() < 1e-6, k
+
+
+def test_ensemble_bead_trajectories_100_steps():
+    lb = _lb()
+    members, starts = ragged_members()
+    ens = lb.Ensemble(members, starts)
+    orcs = [oracle_of(p, pos) for p, pos in zip(members, starts)]
+    for _ in range(10):
+        ens.step(10)
+        for k, orc in enumerate(orcs):
+            advance_like_member(orc, 10, oracle.RUNNING)
+            assert np.abs(ens.beads(k)[0] - orc.beads()[0]).max() < 1e-4, k
+    res = ens.results()
+    # the single bead starts in the pore mouth and crosses within 100 steps
+    assert res["state"][4] == lb.TRANSLOCATED and res["steps"][4] < 100
+    for k, orc in enumerate(orcs):
+        st = orc.status()
+        assert res["steps"][k] == st["step"], k
+        assert res["n_trans"][k] == st["n_trans"] and res["state"][k] == st["state"], k
+        assert res["t_transloc"][k] == st["t_transloc"], k
+
+
+def test_ensemble_matches_single_box_path():
+    """Ensemble realisations against lbmd_step on the same parameters: same
+    kernels, same lane layout, so they agree to float atomics ordering."""
+    lb = _lb()
+    members, starts = ragged_members()
+    ens = lb.Ensemble(members, starts)
+    ens.step(25)
+    for k, (p, pos) in enumerate(zip(members, starts)):
+        sim = lb.Simulation(p, init_pos=pos)
+        advance_like_member(sim, 25, lb.RUNNING)
+        assert rel_err(ens.populations(k), sim.populations().astype(np.float64)) < 1e-6, k
+        assert np.abs(ens.beads(k)[0] - sim.beads()[0]).max() < 1e-6, k
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 2e-4), ("bf16", 2e-3)])
+def test_ensemble_half_storage_matches_single_box(storage, tol):
+    """16-bit storage: the bead sources are added by atomics whose order varies
+    from run to run, and every add rounds to the storage type, so two runs may
+    differ by a storage ulp of the deviation |h| <= 0.005 at the touched nodes:
+    relative to the smallest population 1/36 that is 2^-11 * 0.005 * 36 = 9e-5
+    (fp16) and 2^-8 * 0.005 * 36 = 7e-4 (bf16); the bound is twice that."""
+    lb = _lb()
+    members, starts = ragged_members(storage)
+    ens = lb.Ensemble(members, starts)
+    ens.step(10)
+    for k, (p, pos) in enumerate(zip(members, starts)):
+        sim = lb.Simulation(p, init_pos=pos)
+        advance_like_member(sim, 10, lb.RUNNING)
+        assert rel_err(ens.populations(k), sim.populations().astype(np.float64)) < tol, k
+        assert np.abs(ens.beads(k)[0] - sim.beads()[0]).max() < 1e-4, k
+
+
+def test_ensemble_runs_each_member_to_its_translocation():
+    """Paper-like small boxes translocate in a few hundred steps.  Each member
+    stops at its own completion step, which matches the oracle's within two
+    steps (contractive dynamics at eps = 2e-3); a member that has stopped keeps
+    its state while the others run on."""
+    lb = _lb()
+    members, starts = [], []
+    for seed in range(4):
+        p = si.small_translocation(seed)
+        p["lj_eps"] = PAPER_EPS
+        members.append(p)
+        starts.append(si.saw_chain(p, seed))
+    ens = lb.Ensemble(members, starts)
+    ens.run(1200, check_every=64)
+    res = ens.results()
+    assert ens.live() == 0
+    for k, (p, pos) in enumerate(zip(members, starts)):
+        orc = oracle_of(p, pos)
+        while orc.status()["state"] == oracle.RUNNING and orc.status()["step"] < 1200:
+            orc.step(50)
+        so = orc.status()
+        assert so["state"] == oracle.TRANSLOCATED
+        assert res["state"][k] == lb.TRANSLOCATED
+        assert abs(int(res["t_transloc"][k]) - so["t_transloc"]) <= 2
+        # stopped exactly at its completion step
+        assert res["steps"][k] == res["t_transloc"][k]
+
+
+def test_ensemble_step_cap_and_resume():
+    """run() stops every member at the cap; a higher cap resumes them, also
+    when the member's step parity differs from the ensemble's."""
+    lb = _lb()
+    members, starts = ragged_members()
+    ens = lb.Ensemble(members, starts)
+    ens.run(20, check_every=16)
+    res = ens.results()
+    running = res["state"] == lb.RUNNING
+    assert np.all(res["steps"][running] == 20)
+    ens.run(37, check_every=16)
+    ens.run(50, check_every=16)
+    res = ens.results()
+    for k, (p, pos) in enumerate(zip(members, starts)):
+        if res["state"][k] != lb.RUNNING:
+            continue
+        assert res["steps"][k] == 50
+        sim = lb.Simulation(p, init_pos=pos)
+        advance_like_member(sim, 50, lb.RUNNING)
+        assert rel_err(ens.populations(k), sim.populations().astype(np.float64)) < 1e-6, k
+
+
+def test_ensemble_autotune_leaves_the_state_unchanged():
+    lb = _lb()
+    members, starts = ragged_members()
+    a = lb.Ensemble(members, starts)
+    b = lb.Ensemble(members, starts)
+    a.step(5)
+    ms = a.autotune(trials=2)
+    assert ms > 0
+    t = a.tuning()
+    assert t["rows"] in (4, 8, 16) and t["warps"] in (32, 48) and 1 <= t["claim"] <= 8
+    a.step(6)
+    b.step(11)
+    for k in range(len(members)):
+        assert rel_err(a.populations(k), b.populations(k).astype(np.float64)) < 1e-6, k
+        assert np.abs(a.beads(k)[0] - b.beads(k)[0]).max() < 1e-6, k
+
+
+@pytest.mark.parametrize("rows,warps,claim", [(4, 32, 1), (16, 48, 8), (8, 32, 3)])
+def test_ensemble_tile_shapes_agree(rows, warps, claim):
+    lb = _lb()
+    members, starts = ragged_members()
+    a = lb.Ensemble(members, starts)
+    b = lb.Ensemble(members, starts)
+    a.set_tuning(rows, warps, claim)
+    a.step(7)
+    b.step(7)
+    for k in range(len(members)):
+        assert rel_err(a.populations(k), b.populations(k).astype(np.float64)) < 1e-6, k
+
+
+def test_ensemble_kernel_timing():
+    lb = _lb()
+    members, starts = ragged_members()
+    ens = lb.Ensemble(members, starts)
+    ens.set_kernel_timing(True)
+    ens.step(3)
+    kt = ens.kernel_times()
+    assert kt["steps"] == 3 and 0 < kt["lb_ms"] <= kt["step_ms"]
+    ens.set_kernel_timing(False)
+    ens.step(2)
+    assert ens.results()["steps"].min() == 5  # nobody translocates in 5 steps

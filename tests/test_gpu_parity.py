@@ -91,20 +91,33 @@ def test_stream_collide_1000_steps(forcing):
     assert rel_err(sim.populations(), orc.populations()) < 1e-4
 
 
-def test_storage_precision_variants():
+@pytest.mark.parametrize("case", range(len(LB_CASES)))
+def test_storage_precision_variants(case):
     """FP16 / BF16 deviation storage: h = f - w rho0 of size |h| <= ~0.01 is
     kept with 11 (fp16) or 8 (bf16) significant bits, i.e. an absolute error
     <= 2^-11 * 0.01 (fp16) or 2^-8 * 0.01 (bf16) per rounding; relative to the
     smallest population (1/36) that is <= 2e-4 and 1.2e-3 per step, and the
-    BGK relaxation keeps it from growing over the 10 steps checked."""
-    p = LB_CASES[3]
-    rho, u = si.random_flow((16, 16, 32), seed=5, u_max=0.03)
+    BGK relaxation keeps it from growing over the 10 steps checked.  Boxes with
+    even nx take the paired-node kernel, odd nx the per-node one."""
+    p = LB_CASES[case]
+    shape = (p["nz"], p["ny"], p["nx"])
+    rho, u = si.random_flow(shape, seed=5 + case, u_max=0.03)
     for storage, tol in (("f16", 6e-4), ("bf16", 4e-3)):
         sim, orc = pair(p, init_rho=rho, init_u=u, storage=storage)
         sim.step(10)
         orc.step(10)
         err = rel_err(sim.populations(), orc.populations())
         assert err < tol, (storage, err)
+
+
+@pytest.mark.parametrize("storage,tol,btol", [("f16", 6e-4, 1e-4), ("bf16", 4e-3, 1e-3)])
+def test_coupled_storage_variants(storage, tol, btol):
+    p, pos = small_case(4, lj_eps=2e-3)
+    sim, orc = pair(p, init_pos=pos, storage=storage)
+    sim.step(10)
+    orc.step(10)
+    assert rel_err(sim.populations(), orc.populations()) < tol
+    assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < btol
 
 
 def test_taylor_green_decay_on_gpu():
