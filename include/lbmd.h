@@ -245,7 +245,7 @@ int lbmd_destroy(lbmd_ctx *ctx);
  * gather and the spread over every bead of every realisation, one MD block
  * per chain (chains grouped by block size, the groups run concurrently) and
  * one persistent stream-collide kernel over a shared list of tiles (32 x rows
- * nodes of one z-plane) of every live realisation.  Steps are replayed from
+ * consecutive nodes of one z-plane) of every live realisation.  Steps are replayed from
  * CUDA graphs of 1, 2 and 16 steps.
  *
  * A realisation is live while its state word is LBMD_RUNNING and it has taken
@@ -263,8 +263,8 @@ typedef struct lbmd_ensemble lbmd_ensemble;
 /*
  * Workspace bytes for `count` realisations members[0 .. count-1].  Each member
  * is validated as by lbmd_workspace_size and must further have
- * n_beads >= 1 and 19 * nx*ny*nz < 2^31; all members must share storage and
- * forcing (LBMD_EUNSUPPORTED otherwise).  count must be >= 1.
+ * n_beads >= 1, 19 * nx*ny*nz < 2^31 and nx*ny < 2^22; all members must share
+ * storage and forcing (LBMD_EUNSUPPORTED otherwise).  count must be >= 1.
  */
 int lbmd_ensemble_workspace_size(const lbmd_params *members, int32_t count, size_t *bytes);
 

@@ -25,7 +25,7 @@ constexpr int kEnsBlock = 16;   // steps per long graph
 const int kEnsGraphSteps[3] = {1, 2, kEnsBlock};
 
 struct EnsLayout {
-  size_t mem, tiles, n_tiles, counter, beads, live, cap, chains, stage;
+  size_t mem, lbd, tiles, n_tiles, counter, beads, live, cap, chains, stage;
   size_t stage_floats;
   size_t max_tiles;  // tile capacity (rows = 4, every realisation)
   int nb;            // padded bead slots
@@ -34,8 +34,10 @@ struct EnsLayout {
   size_t total;
 };
 
+// Tiles of 32 x rows consecutive nodes per z-plane.
 size_t tiles_of(const lbmd_params &p, int rows) {
-  return (size_t)((p.nx + 31) / 32) * (size_t)((p.ny + rows - 1) / rows) * (size_t)p.nz;
+  const size_t plane = (size_t)p.nx * p.ny, ts = (size_t)32 * rows;
+  return (plane + ts - 1) / ts * (size_t)p.nz;
 }
 
 int validate_members(const lbmd_params *m, int32_t count) {
@@ -52,6 +54,8 @@ int validate_members(const lbmd_params *m, int32_t count) {
     const long long V = (long long)m[k].nx * m[k].ny * m[k].nz;
     if (19 * ((V + 63) / 64 * 64) >= 0x7fffffffLL)
       return fail(LBMD_EUNSUPPORTED, "member %d: box too large for 32-bit population offsets", k);
+    if ((long long)m[k].nx * m[k].ny >= (1LL << 22))
+      return fail(LBMD_EUNSUPPORTED, "member %d: nx * ny must be < 2^22", k);
     if (m[k].storage != m[0].storage || m[k].forcing != m[0].forcing)
       return fail(LBMD_EUNSUPPORTED, "member %d: storage and forcing must match member 0", k);
   }
@@ -75,6 +79,7 @@ EnsLayout make_ens_layout(const lbmd_params *m, int32_t count) {
     E.stage_floats = std::max(E.stage_floats, stage_floats_for(m[k]));
   }
   E.mem = take((size_t)count * sizeof(EnsMember));
+  E.lbd = take((size_t)count * sizeof(EnsLb));
   E.tiles = take(std::max<size_t>(E.max_tiles, 1) * sizeof(EnsTile));
   E.n_tiles = take(sizeof(int));
   E.counter = take(sizeof(int));
@@ -106,8 +111,10 @@ struct lbmd_ensemble {
   char *ws;
   std::vector<Instance> inst;
   std::vector<EnsMember> hmem;
+  std::vector<EnsLb> hlbd;
   std::vector<Group> groups;
   EnsMember *d_mem;
+  EnsLb *d_lbd;
   EnsTile *d_tiles;
   int *d_n_tiles, *d_counter, *d_live, *d_chains;
   int2 *d_beads;
@@ -167,10 +174,9 @@ cudaError_t upload_tiles(lbmd_ensemble *e, const std::vector<int> &live) {
     if (!live[m]) continue;
     ++n_live;
     const lbmd_params &p = e->p[m];
-    const int ntx = (p.nx + 31) / 32, nby = (p.ny + e->rows - 1) / e->rows;
+    const int plane = p.nx * p.ny, ts = 32 * e->rows;
     for (int z = 0; z < p.nz; ++z)
-      for (int by = 0; by < nby; ++by)
-        for (int bx = 0; bx < ntx; ++bx) e->htiles.push_back(EnsTile{m, bx, by, z});
+      for (int r0 = 0; r0 < plane; r0 += ts) e->htiles.push_back(EnsTile{m, z, r0, 0});
   }
   const int n = (int)e->htiles.size();
   cudaError_t err;
@@ -261,7 +267,7 @@ cudaError_t enqueue_ens_step(lbmd_ensemble *e, int cur) {
   }
   if (t[1] && (err = cudaEventRecord(t[1], e->own)) != cudaSuccess) return err;
   if ((err = launch_ens_stream_collide(e->storage, e->forcing, e->rows, e->warps, e->claim, e->grid,
-                                       e->d_mem, e->d_tiles, e->d_n_tiles, e->d_counter, live, cur,
+                                       e->d_lbd, e->d_tiles, e->d_n_tiles, e->d_counter, live, cur,
                                        e->own)) != cudaSuccess)
     return err;
   if (t[2] && (err = cudaEventRecord(t[2], e->own)) != cudaSuccess) return err;
@@ -379,6 +385,7 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
   e->ws = (char *)dev_workspace;
   e->user = (cudaStream_t)cuda_stream;
   e->d_mem = (EnsMember *)(e->ws + E.mem);
+  e->d_lbd = (EnsLb *)(e->ws + E.lbd);
   e->d_tiles = (EnsTile *)(e->ws + E.tiles);
   e->d_n_tiles = (int *)(e->ws + E.n_tiles);
   e->d_counter = (int *)(e->ws + E.counter);
@@ -418,6 +425,7 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
   // every realisation as a single box in its slice (synchronises per member)
   e->inst.resize(count);
   e->hmem.resize(count);
+  e->hlbd.resize(count);
   for (int m = 0; m < count; ++m) {
     const char *what = "create";
     if ((err = init_instance(members[m], E.L[m], e->ws + E.off[m], e->user, e->inst[m], &what)) !=
@@ -430,6 +438,23 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
     M.ph = e->inst[m].phys;
     M.pop[0] = e->inst[m].pop[0];
     M.pop[1] = e->inst[m].pop[1];
+    EnsLb &D = e->hlbd[m];
+    memset(&D, 0, sizeof(D));
+    const LbGeom &g = e->inst[m].geo;
+    D.pop[0] = M.pop[0];
+    D.pop[1] = M.pop[1];
+    D.lmask = g.lmask;
+    D.tile_near = g.tile_near;
+    D.nx = g.nx;
+    D.ny = g.ny;
+    D.nz = g.nz;
+    D.ntx = g.ntx;
+    D.Vp = (int)g.Vp;
+    D.inv_nx = 1.0f / (float)g.nx;
+    D.omega = M.ph.omega;
+    D.rho0 = M.ph.rho0;
+    for (int a = 0; a < 3; ++a) D.g[a] = M.ph.g[a];
+    D.forcing = M.ph.forcing;
   }
   // (realisation, bead) slots, each realisation padded to a multiple of four
   std::vector<int2> beads;
@@ -456,6 +481,7 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
   const int zero = 0;
   cudaStream_t s = e->user;
   if ((err = cudaMemcpyAsync(e->d_mem, e->hmem.data(), count * sizeof(EnsMember), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(err, "upload");
+  if ((err = cudaMemcpyAsync(e->d_lbd, e->hlbd.data(), count * sizeof(EnsLb), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(err, "upload");
   if ((err = cudaMemcpyAsync(e->d_beads, beads.data(), beads.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(err, "upload");
   if ((err = cudaMemcpyAsync(e->d_chains, chains.data(), chains.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(err, "upload");
   if ((err = cudaMemcpyAsync(e->d_live, live0.data(), live0.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(err, "upload");
@@ -661,7 +687,7 @@ int lbmd_ensemble_autotune(lbmd_ensemble *e, int32_t trials, double *best_ms) {
           if ((err = cudaMemsetAsync(e->d_counter, 0, sizeof(int), e->own)) != cudaSuccess) goto done;
           if (k == 1 && (err = cudaEventRecord(t0, e->own)) != cudaSuccess) goto done;
           if ((err = launch_ens_stream_collide(e->storage, e->forcing, rows, warps, claim, e->sms * per_sm,
-                                               e->d_mem, e->d_tiles, e->d_n_tiles, e->d_counter, live,
+                                               e->d_lbd, e->d_tiles, e->d_n_tiles, e->d_counter, live,
                                                cur, e->own)) != cudaSuccess)
             goto done;
         }

@@ -54,20 +54,19 @@ __device__ __forceinline__ void collide19(float h[kQ], const LbPhys &ph) {
 }
 
 // Stream and collide node (x, y, z) of one box: pull, Eq. 5 collision, store.
+// near: take the bounce-back checks (required if a solid node is within one
+// node of (x, y, z); allowed everywhere).
 template <int S, int FORCING, typename I>
 __device__ __forceinline__ void stream_collide_node(const LbGeom &g, const LbPhys &ph,
                                                     const typename Store<S>::T *__restrict__ src,
                                                     typename Store<S>::T *__restrict__ dst, int x,
-                                                    int y, int z) {
+                                                    int y, int z, bool near) {
   using St = Store<S>;
   const I self = ((I)z * g.ny + y) * g.nx + x;
   float h[kQ];
-  if (tile_is_near(g, x, y, z)) {
-    if (solid_at(g.solid, g.ntx, g.ny, x, y, z)) return;
-    pull19<S, true, I>(g, src, x, y, z, h);
-  } else {
-    pull19<S, false, I>(g, src, x, y, z, h);
-  }
+  const uint32_t bb = near ? __ldg(&g.lmask[self]) : 0u;
+  if (bb & 1u) return;  // solid node
+  pull19_mask<S, I>(g, src, x, y, z, bb, h);
   collide19<FORCING>(h, ph);
   const I Vp = (I)g.Vp;
 #pragma unroll
@@ -86,40 +85,80 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock, 6)
   const int z = blockIdx.z;
   if (bump != nullptr && x == 0 && y == 0 && z == 0) bump->step += 1;
   if (x >= g.nx || y >= g.ny) return;
-  stream_collide_node<S, FORCING, I>(g, ph, src, dst, x, y, z);
+  stream_collide_node<S, FORCING, I>(g, ph, src, dst, x, y, z, tile_is_near(g, x, y, z));
 }
 
 // Ensemble stream-collide: a persistent grid over the tiles of every live
 // realisation.  A block takes `claim` consecutive tiles at a time from a
 // global counter, so blocks that become resident late (after the MD blocks of
-// the same step) simply take fewer tiles.  WARPS is the occupancy the
-// register budget is sized for: 48 warps per SM (40 registers, a little
-// spilling) or 32 (64 registers, none); population offsets are 32-bit.
+// the same step) simply take fewer tiles.  A tile is 32 x ROWS consecutive
+// nodes of one z-plane, so a warp reads and writes one contiguous run of
+// every population whatever the box width (no idle lanes for widths that are
+// not a multiple of 32).  A warp takes the bounce-back checks if any of its
+// nodes needs them.  WARPS is the occupancy the register budget is sized for:
+// 48 warps per SM (40 registers, a little spilling) or 32 (64 registers,
+// none); population offsets are 32-bit.
 template <int S, int FORCING, int ROWS, int WARPS>
 __global__ void __launch_bounds__(32 * ROWS, WARPS / ROWS)
-    k_ens_stream_collide(const EnsMember *__restrict__ mem, const EnsTile *__restrict__ tiles,
+    k_ens_stream_collide(const EnsLb *__restrict__ lbd, const EnsTile *__restrict__ tiles,
                          const int *__restrict__ n_tiles, int *__restrict__ counter,
                          const int *__restrict__ live, int cur, int claim) {
   using T = typename Store<S>::T;
   __shared__ int s_first;
   const int n = *n_tiles;
-  const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
   for (;;) {
-    if (leader) s_first = atomicAdd(counter, claim);
+    if (tid == 0) s_first = atomicAdd(counter, claim);
     __syncthreads();
     const int first = s_first;
     __syncthreads();
     if (first >= n) return;
     const int last = min(first + claim, n);
     for (int t = first; t < last; ++t) {
-      const EnsTile w = tiles[t];
-      if (!live[w.m]) continue;
-      const EnsMember &M = mem[w.m];
-      const LbGeom g = M.a.geo;
-      const int x = w.bx * 32 + threadIdx.x, y = w.by * ROWS + threadIdx.y;
-      if (x < g.nx && y < g.ny)
-        stream_collide_node<S, FORCING, int>(g, M.ph, (const T *)M.pop[cur], (T *)M.pop[cur ^ 1],
-                                             x, y, w.z);
+      const int4 w = __ldg(reinterpret_cast<const int4 *>(tiles) + t);  // (m, z, r0, -)
+      if (!__ldg(&live[w.x])) continue;
+      EnsLb d;
+      {
+        const int4 *q = reinterpret_cast<const int4 *>(lbd + w.x);
+        int4 *o = reinterpret_cast<int4 *>(&d);
+#pragma unroll
+        for (int k = 0; k < (int)(sizeof(EnsLb) / 16); ++k) o[k] = __ldg(q + k);
+      }
+      LbGeom g;
+      g.nx = d.nx;
+      g.ny = d.ny;
+      g.nz = d.nz;
+      g.ntx = d.ntx;
+      g.V = 0;
+      g.Vp = d.Vp;
+      g.solid = nullptr;  // the link mask replaces the bitfield here
+      g.tile_near = d.tile_near;
+      g.lmask = d.lmask;
+      LbPhys ph;
+      ph.omega = d.omega;
+      ph.rho0 = d.rho0;
+      ph.g[0] = d.g[0];
+      ph.g[1] = d.g[1];
+      ph.g[2] = d.g[2];
+      ph.forcing = FORCING;
+      // node of this thread: row-major index r in the plane, its row by a
+      // float reciprocal with a one-step correction (exact for nx * ny < 2^22)
+      const int plane = d.nx * d.ny;
+      const int r = w.z + tid;
+      const bool active = r < plane;
+      int y = __float2int_rz((float)r * d.inv_nx);
+      int x = r - y * d.nx;
+      if (x < 0) {
+        --y;
+        x += d.nx;
+      } else if (x >= d.nx) {
+        ++y;
+        x -= d.nx;
+      }
+      const bool near = __any_sync(0xffffffffu, active && tile_is_near(g, x, y, w.y));
+      const T *src = (const T *)(cur ? d.pop[1] : d.pop[0]);
+      T *dst = (T *)(cur ? d.pop[0] : d.pop[1]);
+      if (active) stream_collide_node<S, FORCING, int>(g, ph, src, dst, x, y, w.y, near);
     }
   }
 }
@@ -157,11 +196,11 @@ cudaError_t launch_lb_stream_collide(int storage, const LbGeom &g, const LbPhys 
 }
 
 template <int S, int FORCING, int ROWS, int WARPS>
-static cudaError_t ens_lb_launch(int claim, int grid, const EnsMember *mem, const EnsTile *tiles,
+static cudaError_t ens_lb_launch(int claim, int grid, const EnsLb *lbd, const EnsTile *tiles,
                                  const int *n_tiles, int *counter, const int *live, int cur,
                                  cudaStream_t s) {
   k_ens_stream_collide<S, FORCING, ROWS, WARPS><<<grid, dim3(32, ROWS), 0, s>>>(
-      mem, tiles, n_tiles, counter, live, cur, claim);
+      lbd, tiles, n_tiles, counter, live, cur, claim);
   return cudaGetLastError();
 }
 
@@ -176,7 +215,7 @@ static int ens_lb_occupancy() {
 
 // Dispatch on (storage, forcing, rows, warps per SM) to one instantiation.
 struct EnsLbFns {
-  cudaError_t (*launch)(int, int, const EnsMember *, const EnsTile *, const int *, int *,
+  cudaError_t (*launch)(int, int, const EnsLb *, const EnsTile *, const int *, int *,
                         const int *, int, cudaStream_t);
   int (*occupancy)();
 };
@@ -203,16 +242,39 @@ static EnsLbFns ens_fns(int storage, int forcing, int rows, int warps) {
 }
 
 cudaError_t launch_ens_stream_collide(int storage, int forcing, int rows, int warps, int claim,
-                                      int grid, const EnsMember *mem, const EnsTile *tiles,
+                                      int grid, const EnsLb *lbd, const EnsTile *tiles,
                                       const int *n_tiles, int *counter, const int *live, int cur,
                                       cudaStream_t s) {
   if (storage < LBMD_STORE_F32 || storage > LBMD_STORE_BF16) return cudaErrorInvalidValue;
-  return ens_fns(storage, forcing, rows, warps).launch(claim, grid, mem, tiles, n_tiles, counter,
+  return ens_fns(storage, forcing, rows, warps).launch(claim, grid, lbd, tiles, n_tiles, counter,
                                                        live, cur, s);
 }
 
 int ens_lb_blocks_per_sm(int storage, int forcing, int rows, int warps) {
   return ens_fns(storage, forcing, rows, warps).occupancy();
+}
+
+// Link mask of every node: bit 0 if the node is solid, bit p (1..18) if its
+// pull source x - c_p (periodic wrap) is solid.
+__global__ void k_link_mask(LbGeom g, uint32_t *__restrict__ mask) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kRowsPerBlock + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  uint32_t bb = solid_at(g.solid, g.ntx, g.ny, x, y, z) ? 1u : 0u;
+#pragma unroll
+  for (int p = 1; p < kQ; ++p) {
+    const int sx = wrapi(x - cx(p), g.nx), sy = wrapi(y - cy(p), g.ny), sz = wrapi(z - cz(p), g.nz);
+    if (solid_at(g.solid, g.ntx, g.ny, sx, sy, sz)) bb |= 1u << p;
+  }
+  mask[((size_t)z * g.ny + y) * g.nx + x] = bb;
+}
+
+cudaError_t launch_link_mask(const LbGeom &g, uint32_t *mask, cudaStream_t s) {
+  dim3 block(32, kRowsPerBlock);
+  dim3 grid(g.ntx, (g.ny + kRowsPerBlock - 1) / kRowsPerBlock, g.nz);
+  k_link_mask<<<grid, block, 0, s>>>(g, mask);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

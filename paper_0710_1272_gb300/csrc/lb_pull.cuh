@@ -10,13 +10,15 @@ namespace lbmd {
 // post-collision buffer `src` (Eq. 5 free streaming, pull form):
 //   h_p(x) = h*_p(x - c_p)      if x - c_p is fluid,
 //   h_p(x) = h*_opp(p)(x)       otherwise (the population that left x towards
-//                               the solid node comes back reversed).
-// CHECK = false skips the solid test (tile known to be far from any solid).
-// I is the index type of the population offsets: int when 19 Vp < 2^31
-// (cheaper address arithmetic), size_t otherwise.
-template <int S, bool CHECK, typename I = size_t>
-__device__ __forceinline__ void pull19(const LbGeom &g, const typename Store<S>::T *__restrict__ src,
-                                       int x, int y, int z, float h[kQ]) {
+//                               the solid node comes back reversed),
+// where bit p of `bb` says whether x - c_p is solid (the node's link mask; 0
+// for a node known to be far from any solid node).  I is the index type of
+// the population offsets: int when 19 Vp < 2^31 (cheaper address
+// arithmetic), size_t otherwise.
+template <int S, typename I = size_t>
+__device__ __forceinline__ void pull19_mask(const LbGeom &g,
+                                            const typename Store<S>::T *__restrict__ src, int x,
+                                            int y, int z, uint32_t bb, float h[kQ]) {
   using St = Store<S>;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int xm = wrap_m1(x, nx), xp = wrap_p1(x, nx);
@@ -24,18 +26,6 @@ __device__ __forceinline__ void pull19(const LbGeom &g, const typename Store<S>:
   const int zm = wrap_m1(z, nz), zp = wrap_p1(z, nz);
   const I self = ((I)z * ny + y) * nx + x;
   const I Vp = (I)g.Vp;
-  // first every solid test (independent loads of the bitfield), then every
-  // population address, so that the 19 population loads are in flight together
-  uint32_t bb = 0;
-  if (CHECK) {
-#pragma unroll
-    for (int p = 1; p < kQ; ++p) {
-      const int sx = cx(p) == 1 ? xm : (cx(p) == -1 ? xp : x);
-      const int sy = cy(p) == 1 ? ym : (cy(p) == -1 ? yp : y);
-      const int sz = cz(p) == 1 ? zm : (cz(p) == -1 ? zp : z);
-      bb |= (uint32_t)solid_at(g.solid, g.ntx, ny, sx, sy, sz) << p;
-    }
-  }
 #pragma unroll
   for (int p = 0; p < kQ; ++p) {
     // source node x - c_p
@@ -46,6 +36,15 @@ __device__ __forceinline__ void pull19(const LbGeom &g, const typename Store<S>:
     const I bidx = (I)opp(p) * Vp + self;
     h[p] = St::load(src + (((bb >> p) & 1u) ? bidx : sidx));
   }
+}
+
+// As pull19_mask; CHECK = false skips the link mask (tile known to be far
+// from any solid node).
+template <int S, bool CHECK, typename I = size_t>
+__device__ __forceinline__ void pull19(const LbGeom &g, const typename Store<S>::T *__restrict__ src,
+                                       int x, int y, int z, float h[kQ]) {
+  const uint32_t bb = CHECK ? __ldg(&g.lmask[((I)z * g.ny + y) * g.nx + x]) : 0u;
+  pull19_mask<S, I>(g, src, x, y, z, bb, h);
 }
 
 // rho - rho0 and the momentum sum_p h_p c_p (sum_p w_p c_p = 0).

@@ -61,6 +61,7 @@ Layout make_layout(const lbmd_params &p, bool with_stage) {
   L.popB = take((size_t)19 * L.Vp * store_bytes(p.storage));
   L.solid = take(rows * L.ntx * sizeof(uint32_t));
   L.tile = take(rows * L.ntx);
+  L.lmask = take((size_t)V * sizeof(uint32_t));
   L.xslab = take((size_t)p.nx);
   L.pos = take(Np * sizeof(float4));
   L.pos_lo = take(Np * sizeof(float4));
@@ -235,11 +236,13 @@ cudaError_t init_instance(const lbmd_params &p, const Layout &L, char *ws, cudaS
   g.Vp = L.Vp;
   g.solid = (const uint32_t *)(ws + L.solid);
   g.tile_near = (const uint8_t *)(ws + L.tile);
+  g.lmask = (const uint32_t *)(ws + L.lmask);
   HostGeometry G;
   build_geometry(p, L.ntx, G);
   UP(cudaMemcpyAsync(ws + L.solid, G.bits.data(), G.bits.size() * 4, cudaMemcpyHostToDevice, s), "upload");
   UP(cudaMemcpyAsync(ws + L.tile, G.tile.data(), G.tile.size(), cudaMemcpyHostToDevice, s), "upload");
   UP(cudaMemcpyAsync(ws + L.xslab, G.xslab.data(), G.xslab.size(), cudaMemcpyHostToDevice, s), "upload");
+  UP(launch_link_mask(g, (uint32_t *)(ws + L.lmask), s), "link mask");
 
   out.phys.omega = (float)(1.0 / p.tau);
   out.phys.rho0 = (float)p.rho0;

@@ -37,6 +37,8 @@ struct LbGeom {
   const uint32_t *solid;        // [nz][ny][ntx] words, bit x & 31 of word x >> 5
   const uint8_t *tile_near;     // [nz][ny][ntx]: 1 if a solid node is within one
                                 // node of the tile's 32 cells (incl. themselves)
+  const uint32_t *lmask;        // [nz][ny][nx] link mask: bit p (1..18) set if the
+                                // pull source x - c_p is solid, bit 0 if x is
 };
 
 struct LbPhys {
@@ -82,10 +84,25 @@ struct EnsMember {
   void *pop[2];     // post-collision populations, swapped every step
 };
 
-// Work item of the ensemble stream-collide: one block-sized tile (32 x rows
-// nodes of one z-plane) of realisation m.
-struct EnsTile {
-  int m, bx, by, z;
+// What the ensemble stream-collide needs of one realisation, 16-byte aligned
+// so that a block reads it with five vector loads.
+struct __align__(16) EnsLb {
+  void *pop[2];                 // post-collision populations, swapped every step
+  const uint32_t *lmask;        // as LbGeom::lmask
+  const uint8_t *tile_near;     // as LbGeom::tile_near
+  int nx, ny, nz, ntx;
+  int Vp;                       // population stride (19 Vp < 2^31)
+  float inv_nx;                 // 1 / nx, for the row of a node in its plane
+  float omega, rho0;
+  float g[3];
+  int forcing;
+};
+
+// Work item of the ensemble stream-collide: 32 x rows consecutive nodes
+// r0 .. r0 + 32 rows - 1 (x fastest, clipped to the plane) of z-plane z of
+// realisation m.
+struct __align__(16) EnsTile {
+  int m, z, r0, pad;
 };
 
 size_t md_smem_bytes(int N);
@@ -97,6 +114,8 @@ cudaError_t md_prepare();
 cudaError_t launch_lb_stream_collide(int storage, const LbGeom &g, const LbPhys &ph,
                                      const void *src, void *dst, DevStatus *bump,
                                      cudaStream_t s);
+// Fill g.lmask from the solid bitfield (once, at set-up).
+cudaError_t launch_link_mask(const LbGeom &g, uint32_t *mask, cudaStream_t s);
 cudaError_t launch_init_populations(int storage, const LbGeom &g, float rho0,
                                     const float *rho, const float *u, float tg_amp,
                                     void *dst, cudaStream_t s);
@@ -116,9 +135,10 @@ cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, cons
 // Stream-collide: persistent grid of `grid` blocks of 32 x rows threads (rows
 // 4, 8 or 16; registers sized for `warps` = 32 or 48 resident warps per SM)
 // taking `claim` tiles at a time from `counter` (reset by the ensemble
-// gather).  Every realisation must have 19 Vp < 2^31 (32-bit offsets).
+// gather).  Every realisation must have 19 Vp < 2^31 (32-bit offsets) and
+// nx * ny < 2^22 (float row division).
 cudaError_t launch_ens_stream_collide(int storage, int forcing, int rows, int warps, int claim,
-                                      int grid, const EnsMember *mem, const EnsTile *tiles,
+                                      int grid, const EnsLb *lbd, const EnsTile *tiles,
                                       const int *n_tiles, int *counter, const int *live, int cur,
                                       cudaStream_t s);
 // Blocks of that kernel that fit on one SM.
