@@ -376,6 +376,12 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
   e->count = count;
   e->storage = members[0].storage;
   e->forcing = members[0].forcing;
+  {
+    bool no_force = true;
+    for (int m = 0; m < count; ++m)
+      for (int a = 0; a < 3; ++a) no_force = no_force && members[m].body_force[a] == 0.0;
+    if (no_force) e->forcing = kForcingNone;  // collision variant of the stream-collide
+  }
   e->p.assign(members, members + count);
   for (auto &q : e->p) {
     q.bond_i = q.bond_j = nullptr;

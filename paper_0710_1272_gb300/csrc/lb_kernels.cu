@@ -18,7 +18,8 @@ constexpr int kRowsPerBlock = 8;  // block = 32 x 8 threads
 //   h*_p = h_p - omega (h_p - heq_p) + S_p,
 //   heq_p = w_p [ (rho - rho0) + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u) ]   (Eq. 6),
 //   paper forcing: S_p = 3 w_p c_p . g;
-//   Guo forcing:   u = (j + g/2)/rho, S_p = (1 - omega/2) w_p [3 (c - u) + 9 (c.u) c] . g.
+//   Guo forcing:   u = (j + g/2)/rho, S_p = (1 - omega/2) w_p [3 (c - u) + 9 (c.u) c] . g;
+//   kForcingNone (g = 0): u = j/rho, S_p = 0.
 template <int FORCING>
 __device__ __forceinline__ void collide19(float h[kQ], const LbPhys &ph) {
   float drho, jx, jy, jz;
@@ -44,10 +45,10 @@ __device__ __forceinline__ void collide19(float h[kQ], const LbPhys &ph) {
     const float cu = cx(p) * ux + cy(p) * uy + cz(p) * uz;
     const float heq = wq(p) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - usq15));
     const float cg = cx(p) * ph.g[0] + cy(p) * ph.g[1] + cz(p) * ph.g[2];
-    float src;
+    float src = 0.f;
     if (FORCING == LBMD_FORCING_GUO)
       src = kguo * wq(p) * (3.0f * (cg - gu) + 9.0f * cu * cg);
-    else
+    else if (FORCING == LBMD_FORCING_PAPER)
       src = 3.0f * wq(p) * cg;
     h[p] = h[p] - om * (h[p] - heq) + src;
   }
@@ -64,9 +65,13 @@ __device__ __forceinline__ void stream_collide_node(const LbGeom &g, const LbPhy
   using St = Store<S>;
   const I self = ((I)z * g.ny + y) * g.nx + x;
   float h[kQ];
-  const uint32_t bb = near ? __ldg(&g.lmask[self]) : 0u;
-  if (bb & 1u) return;  // solid node
-  pull19_mask<S, I>(g, src, x, y, z, bb, h);
+  if (near) {
+    const uint32_t bb = __ldg(&g.lmask[self]);
+    if (bb & 1u) return;  // solid node
+    pull19_mask<S, I>(g, src, x, y, z, bb, h);
+  } else {
+    pull19_mask<S, I>(g, src, x, y, z, 0u, h);  // constant mask: no selects
+  }
   collide19<FORCING>(h, ph);
   const I Vp = (I)g.Vp;
 #pragma unroll
@@ -169,7 +174,9 @@ static cudaError_t lb_launch(const LbGeom &g, const LbPhys &ph, const void *src,
   using T = typename Store<S>::T;
   dim3 block(32, kRowsPerBlock);
   dim3 grid(g.ntx, (g.ny + kRowsPerBlock - 1) / kRowsPerBlock, g.nz);
-  if (ph.forcing == LBMD_FORCING_GUO)
+  if (ph.g[0] == 0.f && ph.g[1] == 0.f && ph.g[2] == 0.f)
+    k_stream_collide<S, kForcingNone, I><<<grid, block, 0, s>>>(g, ph, (const T *)src, (T *)dst, bump);
+  else if (ph.forcing == LBMD_FORCING_GUO)
     k_stream_collide<S, LBMD_FORCING_GUO, I><<<grid, block, 0, s>>>(g, ph, (const T *)src, (T *)dst, bump);
   else
     k_stream_collide<S, LBMD_FORCING_PAPER, I><<<grid, block, 0, s>>>(g, ph, (const T *)src, (T *)dst, bump);
@@ -232,6 +239,7 @@ static EnsLbFns ens_fns_rows(int rows, int warps) {
 }
 template <int S>
 static EnsLbFns ens_fns_store(int forcing, int rows, int warps) {
+  if (forcing == kForcingNone) return ens_fns_rows<S, kForcingNone>(rows, warps);
   if (forcing == LBMD_FORCING_GUO) return ens_fns_rows<S, LBMD_FORCING_GUO>(rows, warps);
   return ens_fns_rows<S, LBMD_FORCING_PAPER>(rows, warps);
 }

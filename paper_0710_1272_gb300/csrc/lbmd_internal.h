@@ -41,6 +41,10 @@ struct LbGeom {
                                 // pull source x - c_p is solid, bit 0 if x is
 };
 
+// Collision variant for a zero body force: both forcing schemes then reduce
+// to plain BGK (no velocity shift, no source term), so the kernels skip them.
+constexpr int kForcingNone = 2;
+
 struct LbPhys {
   float omega;    // 1 / tau
   float rho0;
@@ -137,6 +141,7 @@ cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, cons
 // taking `claim` tiles at a time from `counter` (reset by the ensemble
 // gather).  Every realisation must have 19 Vp < 2^31 (32-bit offsets) and
 // nx * ny < 2^22 (float row division).
+// forcing: LBMD_FORCING_* or kForcingNone (every realisation has g = 0).
 cudaError_t launch_ens_stream_collide(int storage, int forcing, int rows, int warps, int claim,
                                       int grid, const EnsLb *lbd, const EnsTile *tiles,
                                       const int *n_tiles, int *counter, const int *live, int cur,
