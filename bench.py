@@ -9,6 +9,11 @@ spread of the bead impulses.  Metric: MLUPS (all box nodes x steps / s).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The same JSON line carries an "ensemble" object (skip with --no-ensemble):
+512 independent ragged realisations stepped together with FP16 and with FP32
+population storage, against the plain FP32 path stepping one realisation at
+a time -- realisation-steps/s and completed realisations/s to a step cap.
+
 For N > 1 the script runs under torch.distributed (one rank per GPU); every
 rank steps its own independent realisation (different seed) -- weak scaling
 with no collective on the data path; the timed region is bracketed by
@@ -49,6 +54,12 @@ def parse():
                     default="translocation")
     ap.add_argument("--box", type=int, default=256, help="edge of the periodic solvent box")
     ap.add_argument("--tau", type=float, default=1.0)
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the batched-ensemble leg")
+    ap.add_argument("--ens-count", type=int, default=512)
+    ap.add_argument("--ens-steps", type=int, default=400, help="timed ensemble steps")
+    ap.add_argument("--ens-cap", type=int, default=2000,
+                    help="step cap of the run-to-completion comparison")
     return ap.parse_args()
 
 
@@ -290,6 +301,10 @@ def run_ours(args):
     barrier()
     e2e_s = max_over_ranks([time.perf_counter() - t0], dist, "cuda")[0]
 
+    del sim
+    torch.cuda.empty_cache()
+    ens_out = None if args.no_ensemble else ensemble_leg(args, lb, torch, dist, rank, world)
+
     if rank != 0:
         dist.destroy_process_group()
         return 0
@@ -338,12 +353,110 @@ def run_ours(args):
         "clocks": clocks,
         "status": st,
     }
+    if ens_out is not None:
+        line["ensemble"] = ens_out
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, pos, args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def ensemble_leg(args, lb, torch, dist, rank, world):
+    """Batched ragged ensemble (independent translocation realisations, N from
+    {20, 50, 100, 200, 400}, boxes (4 N^0.6, 2 N^0.6, 2 N^0.6) rounded to 16,
+    pore 3 or 5, own seed and self-avoiding start each) stepped in one set of
+    launches per step, FP16 and FP32 storage, against the plain FP32 path that
+    steps one realisation at a time.
+
+    Throughput: `ens_steps` timed steps of every realisation (CUDA events).
+    Completion: every realisation run until it translocates or reaches the
+    step cap `ens_cap` (wall clock, host checks every 256 steps included); the
+    plain path runs one realisation of each (N, pore) class to the same end
+    and is scaled by the class counts."""
+    members, starts = si.ragged_ensemble(args.ens_count, seed=shard_seed(0, rank))
+    cells = sum(m["nx"] * m["ny"] * m["nz"] for m in members)
+    fluid = sum(m["nx"] * m["ny"] * m["nz"] - int(si.solid_mask(m).sum()) for m in members)
+    count = len(members)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    out = {"workload": (f"{count} ragged realisations, N in {{20,50,100,200,400}}, "
+                        f"{cells} nodes, eps={members[0]['lj_eps']}"),
+           "cells": cells}
+    peak, _ = measured_peak_hbm()
+    for storage in ("f16", "f32"):
+        ens = lb.Ensemble([dict(m, storage=storage) for m in members], starts)
+        ens.autotune(2)
+        ens.step(16)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ens.step(args.ens_steps)
+        e1.record()
+        barrier()
+        ms = max_over_ranks([e0.elapsed_time(e1)], dist, "cuda")[0]
+        ens.set_kernel_timing(True)
+        ens.step(20)
+        kt = ens.kernel_times()
+        ens.set_kernel_timing(False)
+        lb_ms = kt["lb_ms"] / max(kt["steps"], 1)
+        achieved = BYTES_PER_NODE[storage] * fluid / (lb_ms / 1e3) / 1e9
+        del ens
+        torch.cuda.empty_cache()
+        # run to completion (translocation or the cap) from a fresh start
+        ens = lb.Ensemble([dict(m, storage=storage) for m in members], starts)
+        ens.autotune(2)
+        barrier()
+        t0 = time.perf_counter()
+        ens.run(args.ens_cap, check_every=256)
+        barrier()
+        wall = max_over_ranks([time.perf_counter() - t0], dist, "cuda")[0]
+        res = ens.results()
+        del ens
+        torch.cuda.empty_cache()
+        out[storage] = {
+            "realisation_steps_per_s": world * count * args.ens_steps / (ms / 1e3),
+            "mlups": world * cells * args.ens_steps / (ms / 1e3) / 1e6,
+            "ms_per_step": ms / args.ens_steps,
+            "stream_collide": {"avg_launch_ms": lb_ms, "achieved_gbs": achieved, "frac": achieved / peak},
+            "completed_per_s": world * count / wall, "completion_wall_s": wall,
+            "translocated": int((res["state"] == 1).sum()),
+        }
+    # plain FP32 path, one realisation at a time: one per (N, pore) class
+    classes = {}
+    for k, m in enumerate(members):
+        classes.setdefault((m["n_beads"], m["pore_d"]), []).append(k)
+    seq_steps_s, seq_total = 0.0, 0.0
+    for (n, d), ks in sorted(classes.items()):
+        k = ks[0]
+        sim = lb.Simulation(dict(members[k], storage="f32"), init_pos=starts[k])
+        sim.step(8)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = 8
+        while done < args.ens_cap and sim.status()["state"] == 0:
+            sim.step(min(256, args.ens_cap - done))
+            done = min(args.ens_cap, done + 256)
+        torch.cuda.synchronize()
+        per_step = (time.perf_counter() - t0) / max(done - 8, 1)
+        seq_total += len(ks) * per_step * done
+        seq_steps_s += len(ks) * per_step
+        del sim
+    out["plain_f32_sequential"] = {
+        "realisation_steps_per_s": count / seq_steps_s,
+        "completed_per_s": count / seq_total,
+        "sample": f"one realisation per (N, pore) class ({len(classes)} classes) run to "
+                  f"translocation or {args.ens_cap} steps, scaled by the class counts",
+    }
+    out["cap_steps"] = args.ens_cap
+    out["f16_vs_plain_f32_completed"] = out["f16"]["completed_per_s"] / out["plain_f32_sequential"]["completed_per_s"]
+    out["f16_vs_f32_ensemble_completed"] = out["f16"]["completed_per_s"] / out["f32"]["completed_per_s"]
+    return out
 
 
 def kernel_rev() -> str:
