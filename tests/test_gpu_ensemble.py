@@ -221,3 +221,36 @@ def test_ensemble_kernel_timing():
     ens.set_kernel_timing(False)
     ens.step(2)
     assert ens.results()["steps"].min() == 5  # nobody translocates in 5 steps
+
+
+def test_translocation_time_statistics_against_oracle_ensemble():
+    """Bead parameters of the benchmark (eps = 1): the dynamics are chaotic, so
+    single realisations of the GPU and of the oracle drift apart; the mean
+    translocation time of an ensemble must still agree.  24 seeds of the
+    N = 20 chain in its 32x16x16 box with a 5x5 pore: the mean t_transloc of
+    the GPU ensemble with FP32, FP16 and BF16 storage lies within the 95%
+    confidence interval (1.96 s / sqrt(n)) of the oracle ensemble's mean."""
+    lb = _lb()
+    members, starts = [], []
+    for s in range(24):
+        p = si.ragged_member(20, 5, seed=1000 + s)
+        members.append(p)
+        starts.append(si.saw_chain(p, p["seed"]))
+    t_orc = []
+    for p, pos in zip(members, starts):
+        orc = oracle_of(p, pos)
+        while orc.status()["state"] == oracle.RUNNING and orc.status()["step"] < 1500:
+            orc.step(25)
+        st = orc.status()
+        assert st["state"] == oracle.TRANSLOCATED
+        t_orc.append(st["t_transloc"])
+    t_orc = np.array(t_orc, dtype=np.float64)
+    half = 1.96 * t_orc.std(ddof=1) / np.sqrt(t_orc.size)
+    for storage in ("f32", "f16", "bf16"):
+        ens = lb.Ensemble([dict(m, storage=storage) for m in members], starts)
+        ens.run(1500, check_every=128)
+        r = ens.results()
+        assert np.all(r["state"] == lb.TRANSLOCATED), storage
+        mean = float(r["t_transloc"].mean())
+        print(f"{storage}: GPU mean {mean:.1f}, oracle mean {t_orc.mean():.1f} +- {half:.1f}")
+        assert abs(mean - t_orc.mean()) <= half, (storage, mean, t_orc.mean(), half)
