@@ -117,14 +117,15 @@ __global__ void __launch_bounds__(32 * ROWS, WARPS / ROWS)
                          const int *__restrict__ n_tiles, int *__restrict__ counter,
                          const int *__restrict__ live, int cur, int claim) {
   using T = typename Store<S>::T;
-  __shared__ int s_first;
+  // two claim slots used alternately: a slot is rewritten two claims later,
+  // after every thread has passed the barrier that follows its read
+  __shared__ int s_first[2];
   const int n = *n_tiles;
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  for (;;) {
-    if (tid == 0) s_first = atomicAdd(counter, claim);
+  for (int slot = 0;; slot ^= 1) {
+    if (tid == 0) s_first[slot] = atomicAdd(counter, claim);
     __syncthreads();
-    const int first = s_first;
-    __syncthreads();
+    const int first = s_first[slot];
     if (first >= n) return;
     const int last = min(first + claim, n);
     for (int t = first; t < last; ++t) {
