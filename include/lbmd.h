@@ -88,6 +88,11 @@ typedef struct lbmd_params {
                                   bond_length; 0: free beads; >0: the bonds
                                   below (must form the linear chain k, k+1) */
   int32_t shake_max_iter;      /* Newton iterations per constraint solve    */
+  int32_t solvent_free;        /* 0: beads coupled to the LB solvent (Sec. II);
+                                  1: no solvent (Sec. III's comparison run):
+                                  u_i = 0, no LB step, no back-reaction; the
+                                  beads keep drag, noise, wall and drive.
+                                  Needs n_beads >= 1.                        */
   double tau;                  /* BGK relaxation time, nu = (tau - 1/2)/3   */
   double rho0;                 /* reference density (paper: 1)              */
   double body_force[3];        /* uniform force density g                   */
@@ -264,7 +269,8 @@ typedef struct lbmd_ensemble lbmd_ensemble;
  * Workspace bytes for `count` realisations members[0 .. count-1].  Each member
  * is validated as by lbmd_workspace_size and must further have
  * n_beads >= 1, 19 * nx*ny*nz < 2^31 and nx*ny < 2^22; all members must share
- * storage and forcing (LBMD_EUNSUPPORTED otherwise).  count must be >= 1.
+ * storage, forcing and solvent_free (LBMD_EUNSUPPORTED otherwise).  count must
+ * be >= 1.
  */
 int lbmd_ensemble_workspace_size(const lbmd_params *members, int32_t count, size_t *bytes);
 
@@ -329,7 +335,8 @@ int lbmd_ensemble_get_tuning(lbmd_ensemble *ens, int32_t *rows, int32_t *warps, 
  * live realisations' current populations, and keeps the fastest shape.  The
  * trial launches write exactly what the next step's stream-collide writes
  * (from the same input), so the simulation is unchanged.  *best_ms (may be
- * NULL) receives the fastest average launch time.  Synchronises.
+ * NULL) receives the fastest average launch time (0 for a solvent-free
+ * ensemble, which has no stream-collide).  Synchronises.
  */
 int lbmd_ensemble_autotune(lbmd_ensemble *ens, int32_t trials, double *best_ms);
 

@@ -56,8 +56,10 @@ int validate_members(const lbmd_params *m, int32_t count) {
       return fail(LBMD_EUNSUPPORTED, "member %d: box too large for 32-bit population offsets", k);
     if ((long long)m[k].nx * m[k].ny >= (1LL << 22))
       return fail(LBMD_EUNSUPPORTED, "member %d: nx * ny must be < 2^22", k);
-    if (m[k].storage != m[0].storage || m[k].forcing != m[0].forcing)
-      return fail(LBMD_EUNSUPPORTED, "member %d: storage and forcing must match member 0", k);
+    if (m[k].storage != m[0].storage || m[k].forcing != m[0].forcing ||
+        m[k].solvent_free != m[0].solvent_free)
+      return fail(LBMD_EUNSUPPORTED,
+                  "member %d: storage, forcing and solvent_free must match member 0", k);
   }
   return LBMD_OK;
 }
@@ -105,7 +107,7 @@ struct Group {  // chains sharing one MD block size
 }  // namespace
 
 struct lbmd_ensemble {
-  int count, storage, forcing;
+  int count, storage, forcing, solvent_free;
   std::vector<lbmd_params> p;  // host pointers cleared
   EnsLayout E;
   char *ws;
@@ -236,7 +238,9 @@ cudaError_t refresh_live(lbmd_ensemble *e) {
   return upload_tiles(e, live);  // synchronises: `live` and `cap` outlive the copies
 }
 
-// One ensemble step reading pop[cur] of every live realisation.
+// One ensemble step reading pop[cur] of every live realisation.  Without a
+// solvent only the MD groups and the spread (bookkeeping: no transfer nodes)
+// run.
 cudaError_t enqueue_ens_step(lbmd_ensemble *e, int cur) {
   cudaError_t err;
   cudaEvent_t t[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -253,7 +257,8 @@ cudaError_t enqueue_ens_step(lbmd_ensemble *e, int cur) {
   const int *live = e->d_live + cur * e->count;
   int *live_next = e->d_live + (cur ^ 1) * e->count;
   if (t[0] && (err = cudaEventRecord(t[0], e->own)) != cudaSuccess) return err;
-  if ((err = launch_ens_gather(e->storage, e->d_mem, e->d_beads, e->E.nb, live, cur, e->d_counter,
+  if (!e->solvent_free &&
+      (err = launch_ens_gather(e->storage, e->d_mem, e->d_beads, e->E.nb, live, cur, e->d_counter,
                                e->own)) != cudaSuccess)
     return err;
   if ((err = cudaEventRecord(e->ev_fork, e->own)) != cudaSuccess) return err;
@@ -266,7 +271,8 @@ cudaError_t enqueue_ens_step(lbmd_ensemble *e, int cur) {
       return err;
   }
   if (t[1] && (err = cudaEventRecord(t[1], e->own)) != cudaSuccess) return err;
-  if ((err = launch_ens_stream_collide(e->storage, e->forcing, e->rows, e->warps, e->claim, e->grid,
+  if (!e->solvent_free &&
+      (err = launch_ens_stream_collide(e->storage, e->forcing, e->rows, e->warps, e->claim, e->grid,
                                        e->d_lbd, e->d_tiles, e->d_n_tiles, e->d_counter, live, cur,
                                        e->own)) != cudaSuccess)
     return err;
@@ -376,6 +382,7 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
   e->count = count;
   e->storage = members[0].storage;
   e->forcing = members[0].forcing;
+  e->solvent_free = members[0].solvent_free;
   {
     bool no_force = true;
     for (int m = 0; m < count; ++m)
@@ -665,6 +672,10 @@ int lbmd_ensemble_autotune(lbmd_ensemble *e, int32_t trials, double *best_ms) {
   int rc = check_ens(e);
   if (rc) return rc;
   if (trials < 1) return fail(LBMD_EINVAL, "trials must be >= 1");
+  if (e->solvent_free) {  // no stream-collide to tune
+    if (best_ms) *best_ms = 0.0;
+    return LBMD_OK;
+  }
   EK(e, cudaEventRecord(e->ev_in, e->user));
   EK(e, cudaStreamWaitEvent(e->own, e->ev_in, 0));
   cudaEvent_t t0, t1;

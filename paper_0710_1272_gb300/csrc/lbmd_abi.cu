@@ -79,6 +79,20 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     for (int k = 0; k < 6; ++k) t[k] = c->tev[c->tev_used + k];
     c->tev_used += 6;
   }
+  if (c->p.solvent_free) {
+    // no solvent (u_i stays 0): the M MD substeps, then the spread, which
+    // finds no transfer node and only advances the step counter
+    if (t[2] && (e = cudaEventRecord(t[2], c->own)) != cudaSuccess) return e;
+    if ((e = launch_md_cycle(c->chain, c->prio_high, c->own)) != cudaSuccess) return e;
+    if (t[3] && (e = cudaEventRecord(t[3], c->own)) != cudaSuccess) return e;
+    for (int k : {0, 1, 4})
+      if (t[k] && (e = cudaEventRecord(t[k], c->own)) != cudaSuccess) return e;
+    if ((e = launch_spread(c->p.storage, c->geo, c->chain.sp_node, c->chain.sp_w, c->chain.J, c->N,
+                           8 * c->N, B, c->status, c->own)) != cudaSuccess)
+      return e;
+    if (t[5] && (e = cudaEventRecord(t[5], c->own)) != cudaSuccess) return e;
+    return cudaSuccess;
+  }
   if (c->N > 0) {
     // (1) gather from the pre-step populations, then fork: the MD cycle runs
     // on the side stream while the stream-collide runs on the main one

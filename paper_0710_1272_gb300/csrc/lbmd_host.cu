@@ -110,6 +110,9 @@ int validate(const lbmd_params *p) {
       return fail(LBMD_EINVAL, "pore origin out of range");
   }
   if (p->y_walls != 0 && p->y_walls != 1) return fail(LBMD_EINVAL, "y_walls must be 0 or 1");
+  if (p->solvent_free != 0 && p->solvent_free != 1)
+    return fail(LBMD_EINVAL, "solvent_free must be 0 or 1");
+  if (p->solvent_free && p->n_beads < 1) return fail(LBMD_EINVAL, "solvent_free needs n_beads >= 1");
   if (p->y_walls && p->ny < 3) return fail(LBMD_EINVAL, "y_walls needs ny >= 3");
   if (p->n_beads < 0 || p->n_beads > LBMD_MAX_BEADS)
     return fail(LBMD_EINVAL, "n_beads must be in [0, %d]", LBMD_MAX_BEADS);

@@ -32,9 +32,9 @@ DEFAULTS = dict(
     tau=1.0, rho0=1.0, body_force=(0.0, 0.0, 0.0),
     bead_mass=1.0, gamma=0.1, kT=1e-4, lj_sigma=1.8, lj_eps=1.0,
     kappa_phi=0.0, f_drive=0.02, bond_len=1.2,
-    shake_tol=1e-6, shake_max_iter=12, init_tg_amp=0.0, seed=0,
+    shake_tol=1e-6, shake_max_iter=12, init_tg_amp=0.0, seed=0, hydrodynamics=1,
 )
-IGNORED_KEYS = {"hydrodynamics", "bonds"}  # oracle-only keys
+IGNORED_KEYS = {"bonds"}  # oracle-only keys
 
 
 class lbmd_params(C.Structure):
@@ -45,6 +45,7 @@ class lbmd_params(C.Structure):
         ("y_walls", C.c_int32), ("storage", C.c_int32), ("forcing", C.c_int32),
         ("coupling", C.c_int32), ("n_beads", C.c_int32), ("md_substeps", C.c_int32),
         ("n_constraints", C.c_int32), ("shake_max_iter", C.c_int32),
+        ("solvent_free", C.c_int32),
         ("tau", C.c_double), ("rho0", C.c_double), ("body_force", C.c_double * 3),
         ("bead_mass", C.c_double), ("gamma", C.c_double), ("kT", C.c_double),
         ("lj_sigma", C.c_double), ("lj_eps", C.c_double), ("kappa_phi", C.c_double),
@@ -154,6 +155,7 @@ def make_params(p: dict, init_pos=None, init_vel=None, init_rho=None, init_u=Non
     for k in ("nx", "ny", "nz", "wall_x", "wall_thickness", "pore_d", "pore_y0", "pore_z0",
               "y_walls", "n_beads", "md_substeps", "shake_max_iter"):
         setattr(cp, k, int(p[k]))
+    cp.solvent_free = 0 if int(p["hydrodynamics"]) else 1  # the oracle's key, inverted
     cp.storage = STORAGE[p["storage"]]
     cp.forcing = FORCING[p["forcing"]]
     cp.coupling = COUPLING[p["coupling"]]

@@ -59,6 +59,7 @@ def test_workspace_covers_two_population_buffers():
     (dict(n_beads=1025), "n_beads"),
     (dict(storage="f64"), None),
     (dict(md_substeps=0), "md_substeps"),
+    (dict(n_beads=0, hydrodynamics=0), "solvent_free"),
 ])
 def test_invalid_parameters_rejected(bad, msg):
     p = dict(si.small_translocation(0, n_beads=4))

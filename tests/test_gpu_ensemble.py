@@ -254,3 +254,28 @@ def test_translocation_time_statistics_against_oracle_ensemble():
         mean = float(r["t_transloc"].mean())
         print(f"{storage}: GPU mean {mean:.1f}, oracle mean {t_orc.mean():.1f} +- {half:.1f}")
         assert abs(mean - t_orc.mean()) <= half, (storage, mean, t_orc.mean(), half)
+
+
+def test_solvent_free_ensemble_matches_oracle():
+    """Without a solvent the ensemble runs the MD groups and the bookkeeping
+    only; each realisation translocates at the oracle's step (eps = 2e-3,
+    within two steps) and stops there."""
+    lb = _lb()
+    members, starts = [], []
+    for n, d, seed in ((20, 3, 31), (20, 5, 32), (50, 5, 33), (37, 3, 34)):
+        p = si.ragged_member(n, d, seed=seed, lj_eps=PAPER_EPS, hydrodynamics=0)
+        members.append(p)
+        starts.append(si.saw_chain(p, p["seed"]))
+    ens = lb.Ensemble(members, starts)
+    assert ens.autotune(1) == 0.0
+    ens.run(6000, check_every=128)
+    r = ens.results()
+    for k, (p, pos) in enumerate(zip(members, starts)):
+        orc = oracle_of(p, pos)
+        while orc.status()["state"] == oracle.RUNNING and orc.status()["step"] < 6000:
+            orc.step(25)
+        so = orc.status()
+        assert so["state"] == oracle.TRANSLOCATED, k
+        assert r["state"][k] == lb.TRANSLOCATED, k
+        assert abs(int(r["t_transloc"][k]) - so["t_transloc"]) <= 2, (k, r["t_transloc"][k], so)
+        assert r["steps"][k] == r["t_transloc"][k]

@@ -384,3 +384,30 @@ def test_paper_sized_box_first_steps():
     orc.step(2)
     assert rel_err(sim.populations(), orc.populations()) < 1e-5
     assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < 1e-5
+
+
+def test_solvent_free_chain_matches_oracle():
+    """Sec. III's comparison run without a solvent: u_i = 0, no LB, no
+    back-reaction; beads keep drag, noise, wall and drive.  One step to 1e-6,
+    100 steps to 1e-4 (eps = 2e-3), the same translocation step, and the
+    populations untouched."""
+    for seed in (0, 1):
+        p, pos = small_case(seed, lj_eps=PAPER_EPS, hydrodynamics=0)
+        sim, orc = pair(p, init_pos=pos)
+        f0 = sim.populations()
+        sim.step(1)
+        orc.step(1)
+        assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < 1e-6
+        for _ in range(99):
+            sim.step(1)
+            orc.step(1)
+        assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < 1e-4
+        assert np.array_equal(sim.populations(), f0)
+        for _ in range(40):
+            if orc.status()["state"] != oracle.RUNNING:
+                break
+            sim.step(25)
+            orc.step(25)
+        sg, so = sim.status(), orc.status()
+        assert so["state"] == oracle.TRANSLOCATED and sg["state"] == so["state"]
+        assert abs(sg["t_transloc"] - so["t_transloc"]) <= 2, (sg, so)
