@@ -1,4 +1,5 @@
-"""Precision report of the 16-bit population storage against the FP64 oracle.
+"""Precision report of the 16-bit population storage against the FP64 oracle,
+and the with/without-solvent comparison of Sec. III.
 
 FP16 and BF16 storage keep the deviations h = f - w_p rho0 in 16 bits; the
 collision and the bead dynamics stay in FP32.  This script measures what that
@@ -15,8 +16,10 @@ costs, next to the FP32 path, and prints a markdown report:
  3. The time-versus-length exponent alpha (mean t ~ N^alpha) at eps = 2e-3
     over N in {50, 100, 200, 400}, 32 seeds per N, from GPU ensembles per
     storage; and over N in {20, 50, 100} on 4 seeds shared with the oracle.
+ 4. The same exponent with and without the solvent (Sec. III compares the
+    two), and the cost of a step with and without it at constant volume.
 
-  python tests/precision_report.py            # needs a CUDA device
+  python tests/precision_report.py [section ...]   # needs a CUDA device; default: all
 
 The oracle ensembles run in a spawn-started process pool (one realisation
 per worker, one thread each) created before the first GPU call.
@@ -172,6 +175,52 @@ def section_alpha(lb, pool):
     print()
 
 
+def section_solvent(lb):
+    print("## 4. With and without the solvent (Sec. III comparison), FP32, eps = 2e-3, 5x5 pore\n")
+    ns = (50, 100, 200, 400)
+    members, starts, which = [], [], []
+    for n in ns:
+        for s in range(32):
+            p = si.ragged_member(n, 5, seed=3000 + 1000 * n + s, lj_eps=2e-3)
+            members.append(p)
+            starts.append(si.saw_chain(p, p["seed"]))
+            which.append(n)
+    which = np.array(which)
+    print("| solvent | " + " | ".join(f"mean t (N={n})" for n in ns) + " | alpha | translocated |")
+    print("|---|" + "---|" * len(ns) + "---|---|")
+    for hydro in (1, 0):
+        ens = lb.Ensemble([dict(m, hydrodynamics=hydro) for m in members], starts)
+        ens.run(400000, check_every=4096)
+        r = ens.results()
+        del ens
+        ok = r["state"] == lb.TRANSLOCATED
+        means = [r["t_transloc"][(which == n) & ok].mean() for n in ns]
+        print(f"| {'LB' if hydro else 'none'} | " + " | ".join(f"{m:.0f}" for m in means) +
+              f" | {alpha_fit(ns, means):.3f} | {ok.sum()}/{len(members)} |")
+    print()
+    import torch
+
+    print("Cost per coupled step at constant volume (256x128x128, one chain), CUDA events:\n")
+    print("| N | with solvent (ms) | without (ms) |")
+    print("|---|---|---|")
+    for n in (50, 100, 400):
+        row = []
+        for hydro in (1, 0):
+            p = si.paper_translocation(0, n_beads=n)
+            p["hydrodynamics"] = hydro
+            sim = lb.Simulation(p, init_pos=si.saw_chain(p, 0))
+            sim.step(50)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(sim.stream)
+            sim.step(500)
+            e1.record(sim.stream)
+            torch.cuda.synchronize()
+            row.append(e0.elapsed_time(e1) / 500)
+            del sim
+        print(f"| {n} | {row[0]:.4f} | {row[1]:.4f} |")
+    print()
+
+
 def main():
     ctx = mp.get_context("spawn")
     with ctx.Pool(processes=max(1, os.cpu_count() or 1)) as pool:
@@ -185,11 +234,17 @@ def main():
             return 1
         import paper_0710_1272_gb300 as lb
 
+        want = set(sys.argv[1:]) or {"1", "2", "3", "4"}
         print("# Precision of 16-bit population storage against the FP64 oracle\n")
         print(f"Device: {torch.cuda.get_device_name(0)}; host cores: {os.cpu_count()}.\n")
-        section_fields(lb, oracle)
-        section_transloc(lb, pool)
-        section_alpha(lb, pool)
+        if "1" in want:
+            section_fields(lb, oracle)
+        if "2" in want:
+            section_transloc(lb, pool)
+        if "3" in want:
+            section_alpha(lb, pool)
+        if "4" in want:
+            section_solvent(lb)
     return 0
 
 
