@@ -98,6 +98,10 @@ def lib():
         L.orc_forces.argtypes = [P, dp, dp]
         L.orc_forces.restype = C.c_double
         L.orc_gather.argtypes = [P, dp, dp]
+        L.orc_diagnostics.argtypes = [P, dp, dp, dp, dp]
+        L.orc_diagnostics.restype = None
+        L.orc_state_diagnostics.argtypes = [P, dp]
+        L.orc_state_diagnostics.restype = None
         L.orc_spread.argtypes = [P, dp, dp, dp]
         L.orc_transfer_weights.argtypes = [P, dp, np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS"), dp]
         L.orc_transfer_weights.restype = C.c_int
@@ -252,6 +256,19 @@ class OracleSim:
         a, b = C.c_int32(), C.c_int32()
         self._L.orc_get_sweeps(self._h, C.byref(a), C.byref(b))
         return a.value, b.value
+
+    def diagnostics(self, pos=None, vel=None, ui=None) -> dict:
+        """Sec. III chain diagnostics (R_U, R_T, R_E, S_H, S_E, K, N_T) of the
+        current state, or of the given positions / velocities / u_i."""
+        out = np.empty(7)
+        if pos is None:
+            self._L.orc_state_diagnostics(self._h, out)
+        else:
+            N = self.p["n_beads"]
+            a = [np.ascontiguousarray(x, dtype=np.float64).reshape(N, 3) for x in (pos, vel, ui)]
+            self._L.orc_diagnostics(self._h, a[0], a[1], a[2], out)
+        return dict(r_u=out[0], r_t=out[1], r_e=out[2], s_h=out[3], s_e=out[4], kinetic=out[5],
+                    n_trans=int(out[6]))
 
     # -- single stages, for the pin tests ---------------------------------
     def forces(self, pos):

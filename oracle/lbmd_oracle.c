@@ -880,6 +880,61 @@ int orc_rattle(const orc_sim *s, const double *r, double *v, int32_t *sweeps) {
   *sweeps = sw;
   return rc;
 }
+/* Chain diagnostics of Sec. III at bead positions r (unwrapped), velocities
+ * v and interpolated fluid velocities ui (3*N each):
+ *   out[0] R_U, out[1] R_T: radii of gyration of the untranslocated
+ *          (x >= x_wall) and translocated (x < x_wall) beads, 0 for an
+ *          empty part;
+ *   out[2] R_E = (R_T^(1/mu) + R_U^(1/mu))^mu, mu = 0.6;
+ *   out[3] S_H = m gamma sum_i v_i . u_i (Eq. 13, the fluid's work rate;
+ *          the paper's unit mass);
+ *   out[4] S_E = sum_i F_drive(r_i) . v_i (Eq. 14);
+ *   out[5] K = m/2 sum_i |v_i|^2;
+ *   out[6] N_T.
+ * Without a wall every bead counts as untranslocated. */
+void orc_diagnostics(const orc_sim *s, const double *r, const double *v, const double *ui,
+                     double out[7]) {
+  const orc_params *p = &s->p;
+  const int N = p->n_beads;
+  double cm[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  int cnt[2] = {0, 0};
+  for (int i = 0; i < N; ++i) {
+    const int t = (p->wall_x >= 0 && r[3 * i] < p->wall_x) ? 1 : 0;
+    cnt[t] += 1;
+    for (int a = 0; a < 3; ++a) cm[t][a] += r[3 * i + a];
+  }
+  for (int t = 0; t < 2; ++t)
+    for (int a = 0; a < 3; ++a) cm[t][a] = cnt[t] ? cm[t][a] / cnt[t] : 0.0;
+  double r2[2] = {0, 0};
+  double sh = 0, se = 0, ke = 0;
+  for (int i = 0; i < N; ++i) {
+    const int t = (p->wall_x >= 0 && r[3 * i] < p->wall_x) ? 1 : 0;
+    double Fd[3] = {0, 0, 0};
+    drive_force(s, &r[3 * i], Fd);
+    for (int a = 0; a < 3; ++a) {
+      const double d = r[3 * i + a] - cm[t][a];
+      r2[t] += d * d;
+      sh += v[3 * i + a] * ui[3 * i + a];
+      se += Fd[a] * v[3 * i + a];
+      ke += v[3 * i + a] * v[3 * i + a];
+    }
+  }
+  const double mu = 0.6;
+  const double RU = cnt[0] ? sqrt(r2[0] / cnt[0]) : 0.0;
+  const double RT = cnt[1] ? sqrt(r2[1] / cnt[1]) : 0.0;
+  out[0] = RU;
+  out[1] = RT;
+  out[2] = pow(pow(RT, 1.0 / mu) + pow(RU, 1.0 / mu), mu);
+  out[3] = p->mass * p->gamma * sh;
+  out[4] = se;
+  out[5] = 0.5 * p->mass * ke;
+  out[6] = cnt[1];
+}
+
+void orc_state_diagnostics(const orc_sim *s, double out[7]) {
+  orc_diagnostics(s, s->r, s->v, s->ui, out);
+}
+
 int orc_weights_table(double w[Q], int32_t c[3 * Q]) {
   for (int p = 0; p < Q; ++p) {
     w[p] = weight(p);
