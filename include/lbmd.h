@@ -93,6 +93,10 @@ typedef struct lbmd_params {
                                   u_i = 0, no LB step, no back-reaction; the
                                   beads keep drag, noise, wall and drive.
                                   Needs n_beads >= 1.                        */
+  int32_t diag_every;          /* record the chain diagnostics (lbmd_diag)
+                                  at the end of every diag_every-th step;
+                                  0: never                                  */
+  int32_t diag_capacity;       /* records kept (later ones are dropped)     */
   double tau;                  /* BGK relaxation time, nu = (tau - 1/2)/3   */
   double rho0;                 /* reference density (paper: 1)              */
   double body_force[3];        /* uniform force density g                   */
@@ -116,6 +120,23 @@ typedef struct lbmd_params {
 } lbmd_params;
 
 typedef struct lbmd_ctx lbmd_ctx; /* opaque */
+
+/*
+ * Chain diagnostics of Sec. III at the end of an LB step.  Untranslocated
+ * beads are those with unwrapped x >= wall_x, translocated ones x < wall_x
+ * (every bead is untranslocated without a wall).
+ */
+typedef struct lbmd_diag {
+  int64_t step;      /* LB steps completed                                   */
+  int32_t n_trans;   /* N_T                                                  */
+  int32_t reserved;
+  double r_u, r_t;   /* radii of gyration of the untranslocated and the
+                        translocated beads (0 for an empty part)             */
+  double r_e;        /* effective radius (R_T^(1/mu) + R_U^(1/mu))^mu, mu = 0.6 */
+  double s_h;        /* m gamma sum_i v_i . u_i: work rate of the fluid (Eq. 13) */
+  double s_e;        /* sum_i F_drive,i . v_i: work rate of the drive (Eq. 14) */
+  double kinetic;    /* m/2 sum_i |v_i|^2                                    */
+} lbmd_diag;
 
 /*
  * Bytes of device workspace lbmd_create needs for these parameters (two
@@ -237,6 +258,15 @@ int lbmd_kernel_times(lbmd_ctx *ctx, double *lb_ms, double *md_ms, double *sprea
 int lbmd_lb_step_noalloc(const lbmd_params *params, const float *f_in, float *f_out,
                          void *cuda_stream);
 
+/*
+ * The diagnostic records written so far (params.diag_every, at most
+ * params.diag_capacity of them), oldest first: copies min(count, max_records)
+ * to `records` (host) and sets *n_records (may be NULL) to the count.
+ * Values are computed in FP32 on the device.  Synchronises.
+ */
+int lbmd_read_diagnostics(lbmd_ctx *ctx, lbmd_diag *records, int32_t max_records,
+                          int32_t *n_records);
+
 /* Release the context's host resources (not the caller's workspace). */
 int lbmd_destroy(lbmd_ctx *ctx);
 
@@ -319,6 +349,8 @@ int lbmd_ensemble_read_beads(lbmd_ensemble *ens, int32_t member, double *pos, do
                              int dst_is_device);
 int lbmd_ensemble_read_populations(lbmd_ensemble *ens, int32_t member, float *f,
                                    int dst_is_device);
+int lbmd_ensemble_read_diagnostics(lbmd_ensemble *ens, int32_t member, lbmd_diag *records,
+                                   int32_t max_records, int32_t *n_records);
 
 /*
  * Launch shape of the ensemble stream-collide: tile height rows (4, 8 or 16),

@@ -638,6 +638,18 @@ int lbmd_ensemble_read_populations(lbmd_ensemble *e, int32_t member, float *f, i
   return LBMD_OK;
 }
 
+int lbmd_ensemble_read_diagnostics(lbmd_ensemble *e, int32_t member, lbmd_diag *records,
+                                   int32_t max_records, int32_t *n_records) {
+  int rc = check_ens(e);
+  if (rc) return rc;
+  if (member < 0 || member >= e->count) return fail(LBMD_EINVAL, "member out of range");
+  EK(e, cudaEventRecord(e->ev_in, e->user));
+  EK(e, cudaStreamWaitEvent(e->own, e->ev_in, 0));
+  const Instance &in = e->inst[member];
+  return copy_diagnostics(in.status, in.chain.diag, e->p[member].diag_capacity, records,
+                          max_records, n_records, e->own);
+}
+
 int lbmd_ensemble_set_tuning(lbmd_ensemble *e, int32_t rows, int32_t warps, int32_t claim) {
   int rc = check_ens(e);
   if (rc) return rc;

@@ -434,6 +434,16 @@ int lbmd_kernel_times(lbmd_ctx *c, double *lb_ms, double *md_ms, double *spread_
   return LBMD_OK;
 }
 
+int lbmd_read_diagnostics(lbmd_ctx *c, lbmd_diag *records, int32_t max_records,
+                          int32_t *n_records) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  CK(c, cudaEventRecord(c->ev_in, c->own));
+  CK(c, cudaStreamWaitEvent(c->user, c->ev_in, 0));
+  return copy_diagnostics(c->status, c->chain.diag, c->p.diag_capacity, records, max_records,
+                          n_records, c->user);
+}
+
 int lbmd_destroy(lbmd_ctx *c) {
   if (!c) return LBMD_OK;
   cudaStreamSynchronize(c->own);

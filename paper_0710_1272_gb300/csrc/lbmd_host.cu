@@ -78,6 +78,7 @@ Layout make_layout(const lbmd_params &p, bool with_stage) {
   L.nl_ref = take(Np * sizeof(float4));
   L.lam = take(Np * sizeof(float));
   L.status = take(sizeof(DevStatus));
+  L.diag = take((size_t)std::max(p.diag_capacity, 0) * sizeof(DevDiag));
   L.stage = with_stage ? take(L.stage_floats * sizeof(float)) : 0;
   L.total = o;
   return L;
@@ -113,6 +114,10 @@ int validate(const lbmd_params *p) {
   if (p->solvent_free != 0 && p->solvent_free != 1)
     return fail(LBMD_EINVAL, "solvent_free must be 0 or 1");
   if (p->solvent_free && p->n_beads < 1) return fail(LBMD_EINVAL, "solvent_free needs n_beads >= 1");
+  if (p->diag_every < 0 || p->diag_capacity < 0)
+    return fail(LBMD_EINVAL, "diag_every and diag_capacity must be >= 0");
+  if (p->diag_every > 0 && (p->n_beads < 1 || p->diag_capacity < 1))
+    return fail(LBMD_EINVAL, "diag_every > 0 needs n_beads >= 1 and diag_capacity >= 1");
   if (p->y_walls && p->ny < 3) return fail(LBMD_EINVAL, "y_walls needs ny >= 3");
   if (p->n_beads < 0 || p->n_beads > LBMD_MAX_BEADS)
     return fail(LBMD_EINVAL, "n_beads must be in [0, %d]", LBMD_MAX_BEADS);
@@ -212,6 +217,37 @@ static void build_geometry(const lbmd_params &p, int ntx, HostGeometry &G) {
     }
 }
 
+
+int copy_diagnostics(const DevStatus *status, const DevDiag *diag, int cap, lbmd_diag *records,
+                     int32_t max_records, int32_t *n_records, cudaStream_t s) {
+  if (max_records < 0 || (max_records > 0 && !records))
+    return fail(LBMD_EINVAL, "records is NULL or max_records < 0");
+  DevStatus st;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(&st, status, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return fail(LBMD_ECUDA, "diagnostics: %s", cudaGetErrorString(e));
+  const int n = std::min(std::min(st.diag_count, cap), max_records);
+  std::vector<DevDiag> h((size_t)std::max(n, 1));
+  if (n > 0 && ((e = cudaMemcpyAsync(h.data(), diag, n * sizeof(DevDiag), cudaMemcpyDeviceToHost, s)) !=
+                    cudaSuccess ||
+                (e = cudaStreamSynchronize(s)) != cudaSuccess))
+    return fail(LBMD_ECUDA, "diagnostics: %s", cudaGetErrorString(e));
+  for (int k = 0; k < n; ++k) {
+    lbmd_diag &r = records[k];
+    r.step = h[k].step;
+    r.n_trans = h[k].n_trans;
+    r.reserved = 0;
+    r.r_u = h[k].r_u;
+    r.r_t = h[k].r_t;
+    r.r_e = h[k].r_e;
+    r.s_h = h[k].s_h;
+    r.s_e = h[k].s_e;
+    r.kinetic = h[k].kinetic;
+  }
+  if (n_records) *n_records = std::min(st.diag_count, cap);
+  return LBMD_OK;
+}
 
 cudaError_t init_instance(const lbmd_params &p, const Layout &L, char *ws, cudaStream_t s,
                           Instance &out, const char **what) {
@@ -319,6 +355,9 @@ cudaError_t init_instance(const lbmd_params &p, const Layout &L, char *ws, cudaS
   a.nl_ref = (float4 *)(ws + L.nl_ref);
   a.lam = (float *)(ws + L.lam);
   a.status = out.status;
+  a.diag = (DevDiag *)(ws + L.diag);
+  a.diag_every = p.diag_every;
+  a.diag_cap = p.diag_capacity;
   const int N = p.n_beads;
   // host staging kept alive until the stream synchronisation below
   std::vector<float4> hp(std::max(N, 1)), hl(std::max(N, 1)), hv(std::max(N, 1)),

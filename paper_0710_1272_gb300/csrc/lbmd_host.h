@@ -24,7 +24,7 @@ inline size_t store_bytes(int storage) { return storage == LBMD_STORE_F32 ? 4 : 
 // Byte offsets of every buffer of one box inside its workspace slice.
 struct Layout {
   size_t popA, popB, solid, tile, lmask, xslab, pos, pos_lo, vel, ui, J, sp_node, sp_w, b0, nl_cnt, wl_cnt,
-      nl_list, wl_list, nl_ref, lam, status, stage;
+      nl_list, wl_list, nl_ref, lam, status, diag, stage;
   size_t stage_floats;  // staging capacity in floats (0 without a staging buffer)
   size_t total;
   long long Vp;
@@ -41,6 +41,10 @@ long long chunk_cells_for(const lbmd_params &p);
 
 int validate(const lbmd_params *p);
 bool params_have_bonds(const lbmd_params &p);
+
+// Copy the diagnostic records of one chain to the host (synchronises s).
+int copy_diagnostics(const DevStatus *status, const DevDiag *diag, int cap, lbmd_diag *records,
+                     int32_t max_records, int32_t *n_records, cudaStream_t s);
 
 // Device views of one initialised box and its chain.
 struct Instance {

@@ -21,6 +21,17 @@ struct DevStatus {
   int nl_builds;         // neighbour-list builds so far (0: none yet)
   int nl_ok;             // 1 if the current lists hold every pair (no overflow)
   int out_buf;           // ensemble: population buffer (0/1) written by the last step
+  int diag_count;        // diagnostic records written
+};
+
+// One record of the Sec. III chain diagnostics (end of an LB step).
+struct DevDiag {
+  long long step;        // LB steps completed
+  int n_trans;           // N_T
+  float r_u, r_t, r_e;   // radii of gyration (untranslocated, translocated, effective)
+  float s_h, s_e;        // work rates of the fluid (Eq. 13) and of the drive (Eq. 14)
+  float kinetic;         // m/2 sum |v|^2
+  int pad;
 };
 
 // Neighbour-list capacities per bead: bead partners and solid nodes within
@@ -77,6 +88,8 @@ struct ChainArgs {
   float4 *nl_ref;           // [N] positions at the last list build
   float *lam;               // [N] SHAKE multipliers of the last substep
   DevStatus *status;
+  DevDiag *diag;            // [diag_cap] diagnostic records
+  int diag_every, diag_cap; // record every diag_every steps (0: never)
 };
 
 // One realisation of an ensemble as every ensemble kernel sees it: its box,

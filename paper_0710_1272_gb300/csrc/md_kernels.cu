@@ -263,6 +263,29 @@ __device__ __forceinline__ F3 all_pair_forces(const ChainArgs &a, int i, float4 
   return F;
 }
 
+// Sec. III pulling force on a bead at the local position rh + rl: -f_drive x
+// inside the channel of the pore cross-section and the x-layers within 1.5
+// nodes of the wall.
+__device__ __forceinline__ F3 drive_force_at(const ChainArgs &a, float4 rh, float4 rl) {
+  const LbGeom &g = a.geo;
+  F3 F{0.f, 0.f, 0.f};
+  if (a.has_wall && a.pore_d > 0 && a.fdrive != 0.f) {
+    int c[3];
+    float sf[3];
+    cell_frac_hl(rh.x, rl.x, a.ox, g.nx, c[0], sf[0]);
+    cell_frac_hl(rh.y, rl.y, a.oy, g.ny, c[1], sf[1]);
+    cell_frac_hl(rh.z, rl.z, a.oz, g.nz, c[2], sf[2]);
+    const int di = wrap_near(c[0] - a.wall_x + g.nx / 2, g.nx) - g.nx / 2;
+    const float dx = (float)di + sf[0] - 0.5f * (float)(a.wall_t - 1);
+    const float half = 0.5f * (float)(a.wall_t - 1) + 1.5f;
+    const float ry = (float)c[1] + sf[1], rz = (float)c[2] + sf[2];
+    if (fabsf(dx) <= half && ry >= a.pore_y0 - 0.5f && ry < a.pore_y0 + a.pore_d - 0.5f &&
+        rz >= a.pore_z0 - 0.5f && rz < a.pore_z0 + a.pore_d - 0.5f)
+      F.x -= a.fdrive;
+  }
+  return F;
+}
+
 // Bending (Eq. 3) and the Sec. III pulling force on bead i.
 __device__ F3 bend_drive_forces(const ChainArgs &a, int i, const float4 *s_rh, const float4 *s_rl) {
   const LbGeom &g = a.geo;
@@ -280,22 +303,33 @@ __device__ F3 bend_drive_forces(const ChainArgs &a, int i, const float4 *s_rh, c
     if (i + 2 < N) F = F + bend_force(b0, bp1, a.kappa, 0);
   }
   // pulling force inside the channel through the pore
-  if (a.has_wall && a.pore_d > 0 && a.fdrive != 0.f) {
-    const float4 rh = s_rh[i], rl = s_rl[i];
-    int c[3];
-    float sf[3];
-    cell_frac_hl(rh.x, rl.x, a.ox, g.nx, c[0], sf[0]);
-    cell_frac_hl(rh.y, rl.y, a.oy, g.ny, c[1], sf[1]);
-    cell_frac_hl(rh.z, rl.z, a.oz, g.nz, c[2], sf[2]);
-    const int di = wrap_near(c[0] - a.wall_x + g.nx / 2, g.nx) - g.nx / 2;
-    const float dx = (float)di + sf[0] - 0.5f * (float)(a.wall_t - 1);
-    const float half = 0.5f * (float)(a.wall_t - 1) + 1.5f;
-    const float ry = (float)c[1] + sf[1], rz = (float)c[2] + sf[2];
-    if (fabsf(dx) <= half && ry >= a.pore_y0 - 0.5f && ry < a.pore_y0 + a.pore_d - 0.5f &&
-        rz >= a.pore_z0 - 0.5f && rz < a.pore_z0 + a.pore_d - 0.5f)
-      F.x -= a.fdrive;
+  return F + drive_force_at(a, s_rh[i], s_rl[i]);
+}
+
+// Sum of K values over the block (every thread gets the sums).  red holds
+// 32 K partials and K results; a result is rewritten only after every thread
+// has passed the next call's first barrier, i.e. has read it.
+template <int K>
+__device__ __forceinline__ void block_sum(float (&v)[K], float *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    for (int m = 16; m > 0; m >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], m);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[warp * K + k] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float t = lane < nw ? red[lane * K + k] : 0.f;
+      for (int m = 16; m > 0; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
+      if (lane == 0) red[32 * K + k] = t;
+    }
   }
-  return F;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = red[32 * K + k];
 }
 
 // Solid nodes around a bead within `radius` (node offsets n with
@@ -621,6 +655,44 @@ __device__ __forceinline__ void md_cycle_body(const ChainArgs &a) {
         } else if (st->max_trans >= 1 && out) {
           st->state = LBMD_RETRACTED;
         }
+      }
+    }
+  }
+  // Sec. III chain diagnostics at the end of every diag_every-th step: radii
+  // of gyration of the translocated (x < x_wall, as N_T) and untranslocated
+  // beads from two block sums (centres, then squared distances), the work
+  // rates of Eqs. 13-14 and the kinetic energy
+  if (a.diag_every > 0 && (step + 1) % a.diag_every == 0) {
+    __shared__ float s_red[32 * 6 + 6];
+    const bool tr = bead && a.has_wall && xrel < 0.f, un = bead && !tr;
+    const F3 r{rh.x + rl.x, rh.y + rl.y, rh.z + rl.z};  // local frame
+    float c[6] = {tr ? r.x : 0.f, tr ? r.y : 0.f, tr ? r.z : 0.f,
+                  un ? r.x : 0.f, un ? r.y : 0.f, un ? r.z : 0.f};
+    block_sum<6>(c, s_red);
+    const int nu = N - nt;
+    const float it = nt > 0 ? 1.0f / (float)nt : 0.f, iu = nu > 0 ? 1.0f / (float)nu : 0.f;
+    const F3 dt_{r.x - c[0] * it, r.y - c[1] * it, r.z - c[2] * it};
+    const F3 du_{r.x - c[3] * iu, r.y - c[4] * iu, r.z - c[5] * iu};
+    const F3 fd = bead ? drive_force_at(a, rh, rl) : F3{0.f, 0.f, 0.f};
+    float q[5] = {tr ? dot(dt_, dt_) : 0.f, un ? dot(du_, du_) : 0.f, bead ? dot(v, ui) : 0.f,
+                  dot(fd, v), bead ? dot(v, v) : 0.f};
+    block_sum<5>(q, s_red);
+    if (i == 0) {
+      DevStatus *st = a.status;
+      const int k = st->diag_count;
+      if (k < a.diag_cap) {
+        DevDiag d;
+        d.step = step + 1;
+        d.n_trans = nt;
+        d.r_t = nt > 0 ? sqrtf(q[0] * it) : 0.f;
+        d.r_u = nu > 0 ? sqrtf(q[1] * iu) : 0.f;
+        d.r_e = powf(powf(d.r_t, 1.0f / 0.6f) + powf(d.r_u, 1.0f / 0.6f), 0.6f);
+        d.s_h = a.mass * a.gamma * q[2];
+        d.s_e = q[3];
+        d.kinetic = 0.5f * a.mass * q[4];
+        d.pad = 0;
+        a.diag[k] = d;
+        st->diag_count = k + 1;
       }
     }
   }

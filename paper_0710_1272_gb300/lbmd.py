@@ -33,6 +33,7 @@ DEFAULTS = dict(
     bead_mass=1.0, gamma=0.1, kT=1e-4, lj_sigma=1.8, lj_eps=1.0,
     kappa_phi=0.0, f_drive=0.02, bond_len=1.2,
     shake_tol=1e-6, shake_max_iter=12, init_tg_amp=0.0, seed=0, hydrodynamics=1,
+    diag_every=0, diag_capacity=0,
 )
 IGNORED_KEYS = {"bonds"}  # oracle-only keys
 
@@ -45,7 +46,7 @@ class lbmd_params(C.Structure):
         ("y_walls", C.c_int32), ("storage", C.c_int32), ("forcing", C.c_int32),
         ("coupling", C.c_int32), ("n_beads", C.c_int32), ("md_substeps", C.c_int32),
         ("n_constraints", C.c_int32), ("shake_max_iter", C.c_int32),
-        ("solvent_free", C.c_int32),
+        ("solvent_free", C.c_int32), ("diag_every", C.c_int32), ("diag_capacity", C.c_int32),
         ("tau", C.c_double), ("rho0", C.c_double), ("body_force", C.c_double * 3),
         ("bead_mass", C.c_double), ("gamma", C.c_double), ("kT", C.c_double),
         ("lj_sigma", C.c_double), ("lj_eps", C.c_double), ("kappa_phi", C.c_double),
@@ -56,6 +57,14 @@ class lbmd_params(C.Structure):
         ("init_rho", C.c_void_p), ("init_u", C.c_void_p),
     ]
 
+
+class lbmd_diag(C.Structure):
+    _fields_ = [("step", C.c_int64), ("n_trans", C.c_int32), ("reserved", C.c_int32),
+                ("r_u", C.c_double), ("r_t", C.c_double), ("r_e", C.c_double),
+                ("s_h", C.c_double), ("s_e", C.c_double), ("kinetic", C.c_double)]
+
+
+DIAG_FIELDS = ("step", "n_trans", "r_u", "r_t", "r_e", "s_h", "s_e", "kinetic")
 
 _lib = None
 
@@ -105,6 +114,8 @@ def load(build_if_missing: bool = True):
                                     C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.lbmd_lb_step_noalloc.argtypes = [C.POINTER(lbmd_params), P, P, P]
     L.lbmd_destroy.argtypes = [P]
+    L.lbmd_read_diagnostics.argtypes = [P, P, C.c_int32, C.POINTER(C.c_int32)]
+    L.lbmd_ensemble_read_diagnostics.argtypes = [P, C.c_int32, P, C.c_int32, C.POINTER(C.c_int32)]
     PI32, PI64, PD = C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_double)
     L.lbmd_ensemble_workspace_size.argtypes = [C.POINTER(lbmd_params), C.c_int32, C.POINTER(C.c_size_t)]
     L.lbmd_ensemble_create.argtypes = [C.POINTER(lbmd_params), C.c_int32, P, C.c_size_t, P, C.POINTER(P)]
@@ -127,7 +138,7 @@ def load(build_if_missing: bool = True):
                  "lbmd_read_populations", "lbmd_read_beads", "lbmd_read_bead_aux", "lbmd_status",
                  "lbmd_set_kernel_timing", "lbmd_lb_kernel_time", "lbmd_destroy", "lbmd_version",
                  "lbmd_solver_stats", "lbmd_kernel_times", "lbmd_lb_step_noalloc",
-                 *ENSEMBLE_FUNCTIONS):
+                 "lbmd_read_diagnostics", "lbmd_ensemble_read_diagnostics", *ENSEMBLE_FUNCTIONS):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -153,7 +164,7 @@ def make_params(p: dict, init_pos=None, init_vel=None, init_rho=None, init_u=Non
     p = full_params(p)
     cp = lbmd_params()
     for k in ("nx", "ny", "nz", "wall_x", "wall_thickness", "pore_d", "pore_y0", "pore_z0",
-              "y_walls", "n_beads", "md_substeps", "shake_max_iter"):
+              "y_walls", "n_beads", "md_substeps", "shake_max_iter", "diag_every", "diag_capacity"):
         setattr(cp, k, int(p[k]))
     cp.solvent_free = 0 if int(p["hydrodynamics"]) else 1  # the oracle's key, inverted
     cp.storage = STORAGE[p["storage"]]
@@ -262,6 +273,28 @@ def lbmd_lb_step_noalloc(params: lbmd_params, f_in_ptr: int, f_out_ptr: int, str
     (pre-collision in, pre-collision out), without any allocation."""
     _check(load().lbmd_lb_step_noalloc(C.byref(params), C.c_void_p(f_in_ptr), C.c_void_p(f_out_ptr),
                                        C.c_void_p(stream_ptr)), "lbmd_lb_step_noalloc")
+
+
+def _diag_dict(recs, n):
+    return {k: np.array([getattr(recs[i], k) for i in range(n)]) for k in DIAG_FIELDS}
+
+
+def lbmd_read_diagnostics(ctx, max_records: int) -> dict:
+    """The chain diagnostic records so far, as a dict of arrays."""
+    recs = (lbmd_diag * max(int(max_records), 1))()
+    n = C.c_int32()
+    _check(load().lbmd_read_diagnostics(ctx, C.cast(recs, C.c_void_p), int(max_records), C.byref(n)),
+           "lbmd_read_diagnostics")
+    return _diag_dict(recs, min(n.value, int(max_records)))
+
+
+def lbmd_ensemble_read_diagnostics(ens, member: int, max_records: int) -> dict:
+    recs = (lbmd_diag * max(int(max_records), 1))()
+    n = C.c_int32()
+    _check(load().lbmd_ensemble_read_diagnostics(ens, int(member), C.cast(recs, C.c_void_p),
+                                                 int(max_records), C.byref(n)),
+           "lbmd_ensemble_read_diagnostics")
+    return _diag_dict(recs, min(n.value, int(max_records)))
 
 
 def lbmd_destroy(ctx) -> None:
@@ -452,6 +485,10 @@ class Simulation:
     def kernel_times(self) -> dict:
         return lbmd_kernel_times(self.ctx)
 
+    def diagnostics(self) -> dict:
+        """Recorded chain diagnostics (params diag_every / diag_capacity)."""
+        return lbmd_read_diagnostics(self.ctx, max(int(self.p["diag_capacity"]), 1))
+
 
 class Ensemble:
     """Many independent realisations (each a params dict with its own box,
@@ -535,3 +572,7 @@ class Ensemble:
 
     def kernel_times(self) -> dict:
         return lbmd_ensemble_kernel_times(self.ens)
+
+    def diagnostics(self, member: int) -> dict:
+        return lbmd_ensemble_read_diagnostics(self.ens, member,
+                                              max(int(self.p[member]["diag_capacity"]), 1))

@@ -16,7 +16,7 @@ import seeded_inputs as si
 
 pytestmark = pytest.mark.gpu
 
-GPU_ONLY = ("storage", "init_tg_amp")
+GPU_ONLY = ("storage", "init_tg_amp", "diag_every", "diag_capacity")
 PAPER_EPS = 2e-3
 
 
@@ -279,3 +279,25 @@ def test_solvent_free_ensemble_matches_oracle():
         assert r["state"][k] == lb.TRANSLOCATED, k
         assert abs(int(r["t_transloc"][k]) - so["t_transloc"]) <= 2, (k, r["t_transloc"][k], so)
         assert r["steps"][k] == r["t_transloc"][k]
+
+
+def test_ensemble_diagnostics_match_single_box():
+    """Per-realisation diagnostic records of the ensemble equal those of the
+    single-box path (same kernel body) to float rounding, and stop with the
+    realisation."""
+    lb = _lb()
+    members, starts = ragged_members()
+    members = [dict(m, diag_every=4, diag_capacity=50) for m in members]
+    ens = lb.Ensemble(members, starts)
+    ens.step(40)
+    res = ens.results()
+    for k, (p, pos) in enumerate(zip(members, starts)):
+        d = ens.diagnostics(k)
+        assert list(d["step"]) == list(range(4, res["steps"][k] + 1, 4)), k
+        sim = lb.Simulation(p, init_pos=pos)
+        advance_like_member(sim, 40, lb.RUNNING)
+        ds = sim.diagnostics()
+        assert list(ds["step"]) == list(d["step"])
+        for key in ("r_u", "r_t", "r_e", "s_h", "s_e", "kinetic"):
+            assert np.allclose(d[key], ds[key], rtol=1e-4, atol=1e-7), (k, key)
+        assert np.array_equal(d["n_trans"], ds["n_trans"])

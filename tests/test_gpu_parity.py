@@ -14,7 +14,7 @@ import seeded_inputs as si
 
 pytestmark = pytest.mark.gpu
 
-GPU_ONLY = ("storage", "init_tg_amp")
+GPU_ONLY = ("storage", "init_tg_amp", "diag_every", "diag_capacity")
 
 
 def _gpu():
@@ -411,3 +411,33 @@ def test_solvent_free_chain_matches_oracle():
         sg, so = sim.status(), orc.status()
         assert so["state"] == oracle.TRANSLOCATED and sg["state"] == so["state"]
         assert abs(sg["t_transloc"] - so["t_transloc"]) <= 2, (sg, so)
+
+
+def test_chain_diagnostics_match_oracle():
+    """Sec. III diagnostics recorded on the device every 5 steps against the
+    oracle's at the same steps (eps = 2e-3, bead positions within 1e-4):
+    radii within 2e-4, S_H, S_E and K within 1e-3 relative (+1e-7), N_T exact;
+    and a full record buffer keeps the first records."""
+    lb = _gpu()
+    p, pos = small_case(3, lj_eps=PAPER_EPS, diag_every=5, diag_capacity=40)
+    sim, orc = pair(p, init_pos=pos)
+    want = []
+    for _ in range(20):
+        orc.step(5)
+        want.append(orc.diagnostics())
+    sim.step(100)
+    got = sim.diagnostics()
+    assert list(got["step"]) == list(range(5, 105, 5))
+    for k, w in enumerate(want):
+        assert got["n_trans"][k] == w["n_trans"]
+        for key in ("r_u", "r_t", "r_e"):
+            assert abs(got[key][k] - w[key]) < 2e-4, (k, key, got[key][k], w[key])
+        for key in ("s_h", "s_e", "kinetic"):
+            assert abs(got[key][k] - w[key]) <= 1e-3 * abs(w[key]) + 1e-7, (k, key, got[key][k], w[key])
+    assert max(got["n_trans"]) > 0 and got["r_t"].max() > 0  # both parts populated
+    # capacity: the first three records of a per-step recording
+    p3 = dict(p, diag_every=1, diag_capacity=3)
+    sim3 = lb.Simulation(p3, init_pos=pos)
+    sim3.step(10)
+    d3 = sim3.diagnostics()
+    assert list(d3["step"]) == [1, 2, 3]
