@@ -18,6 +18,9 @@ costs, next to the FP32 path, and prints a markdown report:
     storage; and over N in {20, 50, 100} on 4 seeds shared with the oracle.
  4. The same exponent with and without the solvent (Sec. III compares the
     two), and the cost of a step with and without it at constant volume.
+ 5. The chain diagnostics of Sec. III over ensembles at two friction values:
+    R_T(t=1) / R_U(t=0), the effective radius over the event, the sign of
+    the fluid's work rate, the mean work rates and the kinetic energy.
 
   python tests/precision_report.py [section ...]   # needs a CUDA device; default: all
 
@@ -221,6 +224,48 @@ def section_solvent(lb):
     print()
 
 
+def section_diagnostics(lb):
+    print("## 5. Chain diagnostics over ensembles (Sec. III), N = 200, eps = 2e-3, FP32\n")
+    print("64 realisations per gamma (96x48x48 box, 5x5 pore), diagnostics every 20 steps; t is "
+          "scaled by each realisation's translocation time.\n")
+    print("| gamma | translocated | mean t | R_T(t=1) / R_U(t=0) | R_E / R_U(0) in t-bins 0.1..0.9 "
+          "| records with S_H > 0 | mean S_H | mean S_E | mean gamma K |")
+    print("|---|---|---|---|---|---|---|---|---|")
+    for gamma in (0.1, 0.5):
+        members, starts = [], []
+        for s in range(64):
+            p = si.ragged_member(200, 5, seed=7000 + s, lj_eps=2e-3, gamma=gamma,
+                                 diag_every=20, diag_capacity=4000)
+            members.append(p)
+            starts.append(si.saw_chain(p, p["seed"]))
+        ens = lb.Ensemble(members, starts)
+        ens.run(80000, check_every=4096)
+        r = ens.results()
+        ratios, bins, sh, se, kin = [], [[] for _ in range(9)], [], [], []
+        for k in range(len(members)):
+            if r["state"][k] != lb.TRANSLOCATED:
+                continue
+            d = ens.diagnostics(k)
+            T = float(r["t_transloc"][k])
+            ru0 = d["r_u"][0]
+            ratios.append(d["r_t"][-1] / ru0)
+            frac = d["step"] / T
+            for b in range(9):
+                sel = np.abs(frac - 0.1 * (b + 1)) < 0.05
+                if sel.any():
+                    bins[b].append(d["r_e"][sel].mean() / ru0)
+            sh.append(d["s_h"])
+            se.append(d["s_e"])
+            kin.append(d["kinetic"])
+        del ens
+        sh, se, kin = np.concatenate(sh), np.concatenate(se), np.concatenate(kin)
+        prof = " ".join(f"{np.mean(b):.2f}" for b in bins)
+        print(f"| {gamma} | {len(ratios)}/64 | {r['t_transloc'][r['state'] == 1].mean():.0f} | "
+              f"{np.mean(ratios):.3f} | {prof} | {100 * (sh > 0).mean():.1f} % | {sh.mean():.2e} | "
+              f"{se.mean():.2e} | {gamma * kin.mean():.2e} |")
+    print()
+
+
 def main():
     ctx = mp.get_context("spawn")
     with ctx.Pool(processes=max(1, os.cpu_count() or 1)) as pool:
@@ -234,7 +279,7 @@ def main():
             return 1
         import paper_0710_1272_gb300 as lb
 
-        want = set(sys.argv[1:]) or {"1", "2", "3", "4"}
+        want = set(sys.argv[1:]) or {"1", "2", "3", "4", "5"}
         print("# Precision of 16-bit population storage against the FP64 oracle\n")
         print(f"Device: {torch.cuda.get_device_name(0)}; host cores: {os.cpu_count()}.\n")
         if "1" in want:
@@ -245,6 +290,8 @@ def main():
             section_alpha(lb, pool)
         if "4" in want:
             section_solvent(lb)
+        if "5" in want:
+            section_diagnostics(lb)
     return 0
 
 
