@@ -346,7 +346,10 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": lb_avg_s * 1e3, "launches_timed": lb_n},
         "e2e": {"value": world * V * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
-                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": N * 48 + 48,
+                # bead positions (hi, lo) and velocities as float4 arrays, 256-B
+                # aligned regions, plus the 56-byte status word
+                "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": (2 * ((16 * N + 255) // 256 * 256) + 16 * N + 56) if N else 56,
                 "api": ("lbmd_step(1) + lbmd_read_beads(host) + lbmd_status per step" if N
                         else "lbmd_step(1) + lbmd_status per step")},
         "gpu_launches": (4 if p["n_beads"] > 0 else 1) * args.steps,

@@ -17,7 +17,8 @@
  *    context return LBMD_ECUDA until it is destroyed.
  *  - The library never allocates device memory.  The caller passes one device
  *    workspace (size from lbmd_workspace_size, 256-byte aligned) and a CUDA
- *    stream; every kernel runs on that stream or on a private second stream
+ *    stream (a context also keeps a small pinned host buffer, 48 n_beads + 64
+ *    bytes, for host read-outs of the beads); every kernel runs on that stream or on a private second stream
  *    that is forked from and joined back into it.  The caller owns the
  *    workspace, the stream and every output buffer.
  *  - Work is asynchronous on the stream unless a function says it
@@ -185,7 +186,9 @@ int lbmd_read_populations(lbmd_ctx *ctx, float *f, int dst_is_device);
 
 /*
  * Bead positions (unwrapped, 3*n_beads doubles [i][xyz]) and velocities.
- * dst_is_device as above.  Either pointer may be NULL.
+ * dst_is_device as above.  Either pointer may be NULL.  A host read-out also
+ * fetches the status word in the same synchronisation, so an lbmd_status
+ * call before the next lbmd_step does not synchronise again.
  */
 int lbmd_read_beads(lbmd_ctx *ctx, double *pos, double *vel, int dst_is_device);
 

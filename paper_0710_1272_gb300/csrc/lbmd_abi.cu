@@ -41,6 +41,11 @@ struct lbmd_ctx {
   long long timed_count;
   DevStatus *status;
   float *stage;
+  // pinned host staging of the host bead read-outs (with the status word,
+  // so that lbmd_status right after needs no second synchronisation)
+  char *pinned;
+  DevStatus status_cache;
+  int status_fresh;  // status_cache is current: no step enqueued since
 };
 
 namespace {
@@ -128,6 +133,11 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
   return cudaSuccess;
 }
 
+// Bytes from the start of the bead positions to the end of the velocities.
+size_t bead_span(const lbmd_ctx *c) {
+  return c->L.vel - c->L.pos + (size_t)std::max(c->N, 1) * sizeof(float4);
+}
+
 cudaError_t capture(lbmd_ctx *c, int start, int nsteps, cudaGraphExec_t *out) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(c->own, cudaStreamCaptureModeThreadLocal);
@@ -161,6 +171,7 @@ void destroy_ctx(lbmd_ctx *c) {
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->own) cudaStreamDestroy(c->own);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
 }
 
@@ -246,6 +257,12 @@ int lbmd_create(const lbmd_params *params, void *dev_workspace, size_t bytes, vo
   c->geo = in.geo;
   c->phys = in.phys;
   c->chain = in.chain;
+  if (c->N > 0 &&
+      cudaHostAlloc((void **)&c->pinned, bead_span(c) + sizeof(DevStatus), cudaHostAllocDefault) !=
+          cudaSuccess) {
+    cudaGetLastError();  // no pinned staging: host read-outs copy pageable
+    c->pinned = nullptr;
+  }
   *out = c;
   return LBMD_OK;
 }
@@ -255,6 +272,7 @@ int lbmd_step(lbmd_ctx *c, int64_t n_steps) {
   if (rc) return rc;
   if (n_steps < 0) return fail(LBMD_EINVAL, "n_steps < 0");
   if (n_steps == 0) return LBMD_OK;
+  c->status_fresh = 0;
   CK(c, cudaEventRecord(c->ev_in, c->user));
   CK(c, cudaStreamWaitEvent(c->own, c->ev_in, 0));
   if (c->timing) {
@@ -338,6 +356,34 @@ static int read_bead_pair(lbmd_ctx *c, double *x, double *y, int dst_is_device, 
   const int N = c->N;
   if (N == 0 || (!x && !y)) return LBMD_OK;
   const ChainArgs &a = c->chain;
+  if (!dst_is_device && !aux && c->pinned) {
+    // the position (hi, lo) and velocity arrays are adjacent in the workspace:
+    // one copy of the span and one of the status word into pinned memory, one
+    // synchronisation, then unwrapped x = origin + hi + lo in double on the host
+    const size_t span = bead_span(c);
+    CK(c, cudaMemcpyAsync(c->pinned, a.pos, span, cudaMemcpyDeviceToHost, c->user));
+    CK(c, cudaMemcpyAsync(c->pinned + span, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                          c->user));
+    CK(c, cudaStreamSynchronize(c->user));
+    const float4 *hp = (const float4 *)c->pinned;
+    const float4 *hl = (const float4 *)(c->pinned + (c->L.pos_lo - c->L.pos));
+    const float4 *hv = (const float4 *)(c->pinned + (c->L.vel - c->L.pos));
+    for (int i = 0; i < N; ++i) {
+      if (x) {
+        x[3 * i] = (double)a.ox + (double)hp[i].x + (double)hl[i].x;
+        x[3 * i + 1] = (double)a.oy + (double)hp[i].y + (double)hl[i].y;
+        x[3 * i + 2] = (double)a.oz + (double)hp[i].z + (double)hl[i].z;
+      }
+      if (y) {
+        y[3 * i] = hv[i].x;
+        y[3 * i + 1] = hv[i].y;
+        y[3 * i + 2] = hv[i].z;
+      }
+    }
+    memcpy(&c->status_cache, c->pinned + span, sizeof(DevStatus));
+    c->status_fresh = 1;
+    return LBMD_OK;
+  }
   double *dx = x, *dy = y;
   if (!dst_is_device) {
     dx = x ? (double *)c->stage : nullptr;
@@ -367,8 +413,12 @@ int lbmd_status(lbmd_ctx *c, int64_t *step, int32_t *n_trans, int32_t *state, in
   int rc = check_ctx(c);
   if (rc) return rc;
   DevStatus st;
-  CK(c, cudaMemcpyAsync(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost, c->user));
-  CK(c, cudaStreamSynchronize(c->user));
+  if (c->status_fresh) {
+    st = c->status_cache;  // copied by the last host bead read-out, no step since
+  } else {
+    CK(c, cudaMemcpyAsync(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost, c->user));
+    CK(c, cudaStreamSynchronize(c->user));
+  }
   if (step) *step = st.step;
   if (n_trans) *n_trans = st.n_trans;
   if (state) *state = st.state;
