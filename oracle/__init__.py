@@ -33,7 +33,7 @@ DEFAULTS = dict(
     n_beads=0, md_substeps=5,
     bead_mass=1.0, gamma=0.1, kT=1e-4, lj_sigma=1.8, lj_eps=1.0,
     kappa_phi=0.0, f_drive=0.02, bond_len=1.2,
-    shake_tol=1e-12, shake_max_iter=10000, seed=0, hydrodynamics=1,
+    shake_tol=1e-12, shake_max_iter=10000, seed=0, hydrodynamics=1, kT_fluid=0.0,
 )
 PARAM_KEYS = tuple(DEFAULTS)
 
@@ -53,7 +53,7 @@ class _Params(C.Structure):
         ("mass", C.c_double), ("gamma", C.c_double), ("kT", C.c_double),
         ("lj_sigma", C.c_double), ("lj_eps", C.c_double),
         ("kappa_phi", C.c_double), ("f_drive", C.c_double),
-        ("shake_tol", C.c_double), ("seed", C.c_uint64),
+        ("shake_tol", C.c_double), ("kT_fluid", C.c_double), ("seed", C.c_uint64),
     ]
 
 
@@ -98,6 +98,11 @@ def lib():
         L.orc_forces.argtypes = [P, dp, dp]
         L.orc_forces.restype = C.c_double
         L.orc_gather.argtypes = [P, dp, dp]
+        L.orc_mode_basis.argtypes = [dp, dp]
+        L.orc_mode_basis.restype = None
+        L.orc_fluct_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_double, C.c_double,
+                                      C.c_double, dp]
+        L.orc_fluct_noise.restype = None
         L.orc_diagnostics.argtypes = [P, dp, dp, dp, dp]
         L.orc_diagnostics.restype = None
         L.orc_state_diagnostics.argtypes = [P, dp]
@@ -154,6 +159,7 @@ def _c_params(p: dict, n_bonds: int) -> _Params:
     cp.lj_sigma, cp.lj_eps = float(p["lj_sigma"]), float(p["lj_eps"])
     cp.kappa_phi, cp.f_drive = float(p["kappa_phi"]), float(p["f_drive"])
     cp.shake_tol, cp.seed = float(p["shake_tol"]), int(p["seed"]) & ((1 << 64) - 1)
+    cp.kT_fluid = float(p["kT_fluid"])
     return cp
 
 
@@ -347,6 +353,21 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 def gauss3(seed: int, bead: int, step: int, substep: int, stream: int = 0) -> np.ndarray:
     xi = np.empty(3)
     lib().orc_gauss3(int(seed) & ((1 << 64) - 1), int(bead), int(step), int(substep), int(stream), xi)
+    return xi
+
+
+def mode_basis():
+    """Weight-orthogonal D3Q19 mode basis e[k][p] and norms b_k."""
+    e, b = np.empty((Q, Q)), np.empty(Q)
+    lib().orc_mode_basis(e, b)
+    return e, b
+
+
+def fluct_noise(seed: int, node: int, step: int, rho: float, tau: float, kT: float) -> np.ndarray:
+    """Thermal source F_p of one node at one LB step."""
+    xi = np.empty(Q)
+    lib().orc_fluct_noise(int(seed) & ((1 << 64) - 1), int(node), int(step), float(rho), float(tau),
+                          float(kT), xi)
     return xi
 
 

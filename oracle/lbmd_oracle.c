@@ -93,6 +93,7 @@ typedef struct {
   double tau, rho0, g[3];
   double mass, gamma, kT, lj_sigma, lj_eps, kappa_phi, f_drive;
   double shake_tol;
+  double kT_fluid;                  /* thermal source F_p of Eq. 5; 0: off */
   uint64_t seed;
 } orc_params;
 
@@ -375,6 +376,9 @@ static void compute_moments(orc_sim *s) {
   }
 }
 
+void orc_fluct_noise(uint64_t seed, uint32_t node, int64_t step, double rho, double tau,
+                     double kT, double xi[Q]);
+
 static void collide_all(orc_sim *s) {
   const int64_t V = s->V;
   const orc_params *p = &s->p;
@@ -384,6 +388,12 @@ static void collide_all(orc_sim *s) {
     double f[Q], out[Q], Fb[3] = {s->F[c], s->F[V + c], s->F[2 * V + c]};
     for (int q = 0; q < Q; ++q) f[q] = s->f[q * V + c];
     orc_collide(f, p->tau, Fb, p->g, p->forcing, out);
+    if (p->kT_fluid > 0) {
+      double rho = 0.0, xi[Q];
+      for (int q = 0; q < Q; ++q) rho += f[q];
+      orc_fluct_noise(p->seed, (uint32_t)c, s->step, rho, p->tau, p->kT_fluid, xi);
+      for (int q = 0; q < Q; ++q) out[q] += xi[q];
+    }
     for (int q = 0; q < Q; ++q) s->fs[q * V + c] = out[q];
   }
 }
@@ -410,6 +420,91 @@ static void stream_all(orc_sim *s) {
             s->f[opposite(q) * V + c] = s->fs[q * V + c];
         }
       }
+}
+
+/* ------------------------------------------------------------------ */
+/* Thermal source F_p of Eq. 5 (fluctuating LB, Adhikari et al. 2005; the */
+/* mode form of Duenweg, Schiller and Ladd 2007): independent Gaussian    */
+/* noise in every non-conserved mode of a weight-orthogonal basis, with   */
+/* the variance that the fluctuation-dissipation theorem fixes for a      */
+/* mode relaxing by the factor (1 - omega) per step.                      */
+/* ------------------------------------------------------------------ */
+/* Row k of the basis evaluated at c_p:
+ * 0: 1; 1-3: c_x, c_y, c_z; 4: c^2 - 1; 5: 3c_x^2 - c^2; 6: c_y^2 - c_z^2;
+ * 7-9: c_x c_y, c_y c_z, c_z c_x; 10-12: (3c^2 - 5) c_x, c_y, c_z;
+ * 13: (c_y^2 - c_z^2) c_x; 14: (c_z^2 - c_x^2) c_y; 15: (c_x^2 - c_y^2) c_z;
+ * 16: 3c^4 - 6c^2 + 1; 17: (2c^2 - 3)(3c_x^2 - c^2); 18: (2c^2 - 3)(c_y^2 - c_z^2). */
+static double mode_row(int k, const int c[3]) {
+  const double x = c[0], y = c[1], z = c[2], c2 = x * x + y * y + z * z;
+  switch (k) {
+    case 0: return 1.0;
+    case 1: return x;
+    case 2: return y;
+    case 3: return z;
+    case 4: return c2 - 1.0;
+    case 5: return 3.0 * x * x - c2;
+    case 6: return y * y - z * z;
+    case 7: return x * y;
+    case 8: return y * z;
+    case 9: return z * x;
+    case 10: return (3.0 * c2 - 5.0) * x;
+    case 11: return (3.0 * c2 - 5.0) * y;
+    case 12: return (3.0 * c2 - 5.0) * z;
+    case 13: return (y * y - z * z) * x;
+    case 14: return (z * z - x * x) * y;
+    case 15: return (x * x - y * y) * z;
+    case 16: return 3.0 * c2 * c2 - 6.0 * c2 + 1.0;
+    case 17: return (2.0 * c2 - 3.0) * (3.0 * x * x - c2);
+    case 18: return (2.0 * c2 - 3.0) * (y * y - z * z);
+  }
+  return 0.0;
+}
+
+/* e[k][p] and the norms b_k = sum_p w_p e[k][p]^2. */
+void orc_mode_basis(double e[Q][Q], double b[Q]) {
+  for (int k = 0; k < Q; ++k) {
+    b[k] = 0.0;
+    for (int q = 0; q < Q; ++q) {
+      e[k][q] = mode_row(k, CV[q]);
+      b[k] += weight(q) * e[k][q] * e[k][q];
+    }
+  }
+}
+
+/* Fifteen standard normals for node `node` at LB step `step`: Box-Muller
+ * on both pairs of uniforms of four Philox blocks, counter (node, step lo,
+ * step hi, block | 2 << 8), key (seed lo, seed hi). */
+static void fluct_normals(uint64_t seed, uint32_t node, int64_t step, double r[16]) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  const double two_pi = 6.283185307179586476925286766559;
+  for (uint32_t j = 0; j < 4; ++j) {
+    uint32_t ctr[4] = {node, (uint32_t)(uint64_t)step, (uint32_t)((uint64_t)step >> 32), j | (2u << 8)};
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, key, x);
+    for (int h = 0; h < 2; ++h) {
+      const double u1 = uniform23(x[2 * h]), u2 = uniform23(x[2 * h + 1]);
+      const double rad = sqrt(-2.0 * log(u1));
+      r[4 * j + 2 * h] = rad * cos(two_pi * u2);
+      r[4 * j + 2 * h + 1] = rad * sin(two_pi * u2);
+    }
+  }
+}
+
+/* Thermal source of one node with density rho:
+ *   xi_p = w_p sum_{k=4}^{18} e_kp / b_k * sqrt(mu b_k (1 - (1 - omega)^2)) r_k,
+ *   mu = rho kT / c_s^2, omega = 1 / tau, r_k = normal number k - 4. */
+void orc_fluct_noise(uint64_t seed, uint32_t node, int64_t step, double rho, double tau,
+                     double kT, double xi[Q]) {
+  double e[Q][Q], b[Q], r[16];
+  orc_mode_basis(e, b);
+  fluct_normals(seed, node, step, r);
+  const double g1 = 1.0 - 1.0 / tau;
+  const double mu = rho * kT / CS2;
+  for (int q = 0; q < Q; ++q) xi[q] = 0.0;
+  for (int k = 4; k < Q; ++k) {
+    const double amp = sqrt(mu * b[k] * (1.0 - g1 * g1)) * r[k - 4] / b[k];
+    for (int q = 0; q < Q; ++q) xi[q] += weight(q) * e[k][q] * amp;
+  }
 }
 
 /* ------------------------------------------------------------------ */
