@@ -110,7 +110,10 @@ typedef struct lbmd_params {
   double bond_length;          /* b (paper: 1.2) for n_constraints == -1    */
   double shake_tol;            /* max |d^2 - b^2| / b^2 accepted            */
   double init_tg_amp;          /* Taylor-Green amplitude if init_u == NULL  */
-  uint64_t seed;               /* Philox key of the bead noise              */
+  double kT_fluid;             /* temperature of the thermal source F_p of
+                                  Eq. 5 (fluctuating LB); 0: no source.
+                                  Single-box contexts only.                 */
+  uint64_t seed;               /* Philox key of the bead and fluid noise    */
   const int32_t *bond_i;       /* host, n_constraints entries               */
   const int32_t *bond_j;
   const double *bond_len;
@@ -241,7 +244,8 @@ int lbmd_kernel_times(lbmd_ctx *ctx, double *lb_ms, double *md_ms, double *sprea
  * no context and no workspace and allocates nothing.  The paper has no
  * counterpart: this is a convenience of this library.
  *   params:  box, wall/pore geometry, y_walls, tau, rho0, body_force, forcing;
- *            storage must be LBMD_STORE_F32 and n_beads 0 (other fields ignored)
+ *            storage must be LBMD_STORE_F32, n_beads 0 and kT_fluid 0
+ *            (LBMD_EUNSUPPORTED otherwise; other fields ignored)
  *   f_in:    device, 19*V floats [19][z][y][x], the pre-collision populations
  *            f_p(x, t) (absolute values, not deviations); solid nodes ignored
  *   f_out:   device, 19*V floats, receives f_p(x, t+1); solid nodes set to 0;
@@ -301,9 +305,9 @@ typedef struct lbmd_ensemble lbmd_ensemble;
 /*
  * Workspace bytes for `count` realisations members[0 .. count-1].  Each member
  * is validated as by lbmd_workspace_size and must further have
- * n_beads >= 1, 19 * nx*ny*nz < 2^31 and nx*ny < 2^22; all members must share
- * storage, forcing and solvent_free (LBMD_EUNSUPPORTED otherwise).  count must
- * be >= 1.
+ * n_beads >= 1, 19 * nx*ny*nz < 2^31, nx*ny < 2^22 and kT_fluid = 0; all
+ * members must share storage, forcing and solvent_free (LBMD_EUNSUPPORTED
+ * otherwise).  count must be >= 1.
  */
 int lbmd_ensemble_workspace_size(const lbmd_params *members, int32_t count, size_t *bytes);
 

@@ -54,6 +54,8 @@ int validate_members(const lbmd_params *m, int32_t count) {
     const long long V = (long long)m[k].nx * m[k].ny * m[k].nz;
     if (19 * ((V + 63) / 64 * 64) >= 0x7fffffffLL)
       return fail(LBMD_EUNSUPPORTED, "member %d: box too large for 32-bit population offsets", k);
+    if (m[k].kT_fluid != 0.0)
+      return fail(LBMD_EUNSUPPORTED, "member %d: the thermal source is single-box only", k);
     if ((long long)m[k].nx * m[k].ny >= (1LL << 22))
       return fail(LBMD_EUNSUPPORTED, "member %d: nx * ny must be < 2^22", k);
     if (m[k].storage != m[0].storage || m[k].forcing != m[0].forcing ||

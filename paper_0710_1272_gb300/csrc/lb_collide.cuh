@@ -1,0 +1,151 @@
+// lb_collide.cuh -- the D3Q19 collision of Eq. 5 (BGK relaxation to the Eq. 6
+// equilibrium, body-force source, optional thermal source F_p) and the update
+// of one node (pull streaming + collision + store), shared by the
+// stream-collide kernels.
+#pragma once
+
+#include "lb_pull.cuh"
+
+namespace lbmd {
+
+constexpr int kRowsPerBlock = 8;  // block = 32 x 8 threads
+
+// Weight-orthogonal D3Q19 mode basis, row k at velocity c_p:
+// 0: 1; 1-3: c_x, c_y, c_z; 4: c^2 - 1; 5: 3c_x^2 - c^2; 6: c_y^2 - c_z^2;
+// 7-9: c_x c_y, c_y c_z, c_z c_x; 10-12: (3c^2 - 5) c_x, c_y, c_z;
+// 13: (c_y^2 - c_z^2) c_x; 14: (c_z^2 - c_x^2) c_y; 15: (c_x^2 - c_y^2) c_z;
+// 16: 3c^4 - 6c^2 + 1; 17: (2c^2 - 3)(3c_x^2 - c^2); 18: (2c^2 - 3)(c_y^2 - c_z^2).
+__host__ __device__ constexpr int mode_row(int k, int p) {
+  const int x = cx(p), y = cy(p), z = cz(p), c2 = x * x + y * y + z * z;
+  return k == 0 ? 1 : k == 1 ? x : k == 2 ? y : k == 3 ? z
+       : k == 4 ? c2 - 1 : k == 5 ? 3 * x * x - c2 : k == 6 ? y * y - z * z
+       : k == 7 ? x * y : k == 8 ? y * z : k == 9 ? z * x
+       : k == 10 ? (3 * c2 - 5) * x : k == 11 ? (3 * c2 - 5) * y : k == 12 ? (3 * c2 - 5) * z
+       : k == 13 ? (y * y - z * z) * x : k == 14 ? (z * z - x * x) * y
+       : k == 15 ? (x * x - y * y) * z : k == 16 ? 3 * c2 * c2 - 6 * c2 + 1
+       : k == 17 ? (2 * c2 - 3) * (3 * x * x - c2) : (2 * c2 - 3) * (y * y - z * z);
+}
+
+// Thermal source F_p of Eq. 5 (fluctuating LB, Adhikari et al. 2005, in the
+// mode form of Duenweg, Schiller and Ladd 2007) at node `node`, density rho:
+//   xi_p = w_p sum_{k=4}^{18} e_kp a_k sqrt(rho) r_k,
+//   a_k = sqrt((kT / c_s^2) (1 - (1 - omega)^2) / b_k)   (ph.fl_amp[k - 4]),
+// with fifteen standard normals r_k from Box-Muller on four Philox blocks,
+// counter (node, step lo, step hi, block | 2 << 8), key (seed lo, seed hi).
+// The noise touches only non-conserved modes: mass and momentum are exact.
+__device__ __forceinline__ void thermal_source(const LbPhys &ph, uint32_t node, float rho,
+                                               float xi[kQ]) {
+  const long long step = *ph.step;
+  float r[16];
+#pragma unroll
+  for (uint32_t j = 0; j < 4; ++j) {
+    const U4 c{node, (uint32_t)(unsigned long long)step, (uint32_t)((unsigned long long)step >> 32),
+               j | (2u << 8)};
+    const U4 x = philox4x32_10(c, (uint32_t)ph.seed, (uint32_t)(ph.seed >> 32));
+    const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float rad = sqrtf(-2.0f * logf(uniform23(xs[2 * h])));
+      float sn, cs;
+      sincospif(2.0f * uniform23(xs[2 * h + 1]), &sn, &cs);
+      r[4 * j + 2 * h] = rad * cs;
+      r[4 * j + 2 * h + 1] = rad * sn;
+    }
+  }
+  const float sr = sqrtf(rho);
+  float t[15];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) t[k] = ph.fl_amp[k] * sr * r[k];
+#pragma unroll
+  for (int p = 0; p < kQ; ++p) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 4; k < kQ; ++k)
+      if (mode_row(k, p) != 0) acc = fmaf((float)mode_row(k, p), t[k - 4], acc);
+    xi[p] = wq(p) * acc;
+  }
+}
+
+// Post-collision deviation of every population of one node from its
+// pre-collision deviations (Eq. 5, omega = 1/tau, Delta t = 1):
+//   h*_p = (1 - omega) h_p + omega heq_p + S_p,
+//   heq_p = w_p [ (rho - rho0) + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u) ]   (Eq. 6),
+//   paper forcing: S_p = 3 w_p c_p . g;
+//   Guo forcing:   u = (j + g/2)/rho, S_p = (1 - omega/2) w_p [3 (c - u) + 9 (c.u) c] . g;
+//   kForcingNone (g = 0): u = j/rho, S_p = 0;
+//   FLUCT: plus the thermal source F_p of Eq. 5 (thermal_source).
+// Opposite directions p, opp(p) = p + 1 (odd p) share c.u up to the sign, so
+// heq splits into the even part w_p [(rho - rho0) - 3/2 rho u.u + 9/2 rho (c.u)^2]
+// and the odd part +-3 w_p rho c.u, computed once per pair.
+template <int FORCING, bool FLUCT = false>
+__device__ __forceinline__ void collide19(float h[kQ], const LbPhys &ph, uint32_t node = 0) {
+  float drho, jx, jy, jz;
+  moments19(h, drho, jx, jy, jz);
+  const float rho = ph.rho0 + drho;
+  const float inv = __frcp_rn(rho);  // correctly rounded, as 1.0f / rho
+  float ux, uy, uz;
+  if (FORCING == LBMD_FORCING_GUO) {
+    ux = (jx + 0.5f * ph.g[0]) * inv;
+    uy = (jy + 0.5f * ph.g[1]) * inv;
+    uz = (jz + 0.5f * ph.g[2]) * inv;
+  } else {
+    ux = jx * inv;
+    uy = jy * inv;
+    uz = jz * inv;
+  }
+  const float om = ph.omega, om1 = 1.0f - om;
+  const float A = drho - 1.5f * rho * (ux * ux + uy * uy + uz * uz);
+  const float r3 = 3.0f * rho, r45 = 4.5f * rho;
+  const float gu = ph.g[0] * ux + ph.g[1] * uy + ph.g[2] * uz;
+  const float kguo = 1.0f - 0.5f * om;
+  auto source = [&](int p, float cu) {
+    const float cg = cx(p) * ph.g[0] + cy(p) * ph.g[1] + cz(p) * ph.g[2];
+    if (FORCING == LBMD_FORCING_GUO) return kguo * wq(p) * (3.0f * (cg - gu) + 9.0f * cu * cg);
+    if (FORCING == LBMD_FORCING_PAPER) return 3.0f * wq(p) * cg;
+    return 0.f;
+  };
+  float xi[kQ];
+  if (FLUCT) thermal_source(ph, node, rho, xi);
+  h[0] = om1 * h[0] + (om * wq(0)) * A + source(0, 0.f);
+  if (FLUCT) h[0] += xi[0];
+#pragma unroll
+  for (int p = 1; p < kQ; p += 2) {
+    const float cu = cx(p) * ux + cy(p) * uy + cz(p) * uz;  // c_opp(p) . u = -cu
+    const float even = fmaf(r45 * cu, cu, A);
+    const float odd = r3 * cu;
+    const float ow = om * wq(p);
+    h[p] = fmaf(ow, even + odd, om1 * h[p]) + source(p, cu);
+    h[p + 1] = fmaf(ow, even - odd, om1 * h[p + 1]) + source(p + 1, -cu);
+    if (FLUCT) {
+      h[p] += xi[p];
+      h[p + 1] += xi[p + 1];
+    }
+  }
+}
+
+// Stream and collide node (x, y, z) of one box: pull, Eq. 5 collision, store.
+// near: take the bounce-back checks (required if a solid node is within one
+// node of (x, y, z); allowed everywhere).
+template <int S, int FORCING, typename I, bool FLUCT = false>
+__device__ __forceinline__ void stream_collide_node(const LbGeom &g, const LbPhys &ph,
+                                                    const typename Store<S>::T *__restrict__ src,
+                                                    typename Store<S>::T *__restrict__ dst, int x,
+                                                    int y, int z, bool near) {
+  using St = Store<S>;
+  const I self = ((I)z * g.ny + y) * g.nx + x;
+  float h[kQ];
+  if (near) {
+    const uint32_t bb = __ldg(&g.lmask[self]);
+    if (bb & 1u) return;  // solid node
+    pull19_mask<S, I>(g, src, x, y, z, bb, h);
+  } else {
+    pull19_mask<S, I>(g, src, x, y, z, 0u, h);  // constant mask: no selects
+  }
+  collide19<FORCING, FLUCT>(h, ph, (uint32_t)self);
+  const I Vp = (I)g.Vp;
+#pragma unroll
+  for (int p = 0; p < kQ; ++p) St::store(dst + (I)p * Vp + self, h[p]);
+}
+
+
+}  // namespace lbmd

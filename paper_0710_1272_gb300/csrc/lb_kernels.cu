@@ -7,84 +7,9 @@
 // the 19 loads and 19 stores of a warp is a contiguous 128-byte (fp32) or
 // 64-byte (16-bit) segment; the loads for c_x = +-1 are shifted by one element
 // and are served from L1/L2 for the neighbouring warp's sector.
-#include "lb_pull.cuh"
+#include "lb_collide.cuh"
 
 namespace lbmd {
-
-constexpr int kRowsPerBlock = 8;  // block = 32 x 8 threads
-
-// Post-collision deviation of every population of one node from its
-// pre-collision deviations (Eq. 5, omega = 1/tau, Delta t = 1):
-//   h*_p = (1 - omega) h_p + omega heq_p + S_p,
-//   heq_p = w_p [ (rho - rho0) + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u) ]   (Eq. 6),
-//   paper forcing: S_p = 3 w_p c_p . g;
-//   Guo forcing:   u = (j + g/2)/rho, S_p = (1 - omega/2) w_p [3 (c - u) + 9 (c.u) c] . g;
-//   kForcingNone (g = 0): u = j/rho, S_p = 0.
-// Opposite directions p, opp(p) = p + 1 (odd p) share c.u up to the sign, so
-// heq splits into the even part w_p [(rho - rho0) - 3/2 rho u.u + 9/2 rho (c.u)^2]
-// and the odd part +-3 w_p rho c.u, computed once per pair.
-template <int FORCING>
-__device__ __forceinline__ void collide19(float h[kQ], const LbPhys &ph) {
-  float drho, jx, jy, jz;
-  moments19(h, drho, jx, jy, jz);
-  const float rho = ph.rho0 + drho;
-  const float inv = __frcp_rn(rho);  // correctly rounded, as 1.0f / rho
-  float ux, uy, uz;
-  if (FORCING == LBMD_FORCING_GUO) {
-    ux = (jx + 0.5f * ph.g[0]) * inv;
-    uy = (jy + 0.5f * ph.g[1]) * inv;
-    uz = (jz + 0.5f * ph.g[2]) * inv;
-  } else {
-    ux = jx * inv;
-    uy = jy * inv;
-    uz = jz * inv;
-  }
-  const float om = ph.omega, om1 = 1.0f - om;
-  const float A = drho - 1.5f * rho * (ux * ux + uy * uy + uz * uz);
-  const float r3 = 3.0f * rho, r45 = 4.5f * rho;
-  const float gu = ph.g[0] * ux + ph.g[1] * uy + ph.g[2] * uz;
-  const float kguo = 1.0f - 0.5f * om;
-  auto source = [&](int p, float cu) {
-    const float cg = cx(p) * ph.g[0] + cy(p) * ph.g[1] + cz(p) * ph.g[2];
-    if (FORCING == LBMD_FORCING_GUO) return kguo * wq(p) * (3.0f * (cg - gu) + 9.0f * cu * cg);
-    if (FORCING == LBMD_FORCING_PAPER) return 3.0f * wq(p) * cg;
-    return 0.f;
-  };
-  h[0] = om1 * h[0] + (om * wq(0)) * A + source(0, 0.f);
-#pragma unroll
-  for (int p = 1; p < kQ; p += 2) {
-    const float cu = cx(p) * ux + cy(p) * uy + cz(p) * uz;  // c_opp(p) . u = -cu
-    const float even = fmaf(r45 * cu, cu, A);
-    const float odd = r3 * cu;
-    const float ow = om * wq(p);
-    h[p] = fmaf(ow, even + odd, om1 * h[p]) + source(p, cu);
-    h[p + 1] = fmaf(ow, even - odd, om1 * h[p + 1]) + source(p + 1, -cu);
-  }
-}
-
-// Stream and collide node (x, y, z) of one box: pull, Eq. 5 collision, store.
-// near: take the bounce-back checks (required if a solid node is within one
-// node of (x, y, z); allowed everywhere).
-template <int S, int FORCING, typename I>
-__device__ __forceinline__ void stream_collide_node(const LbGeom &g, const LbPhys &ph,
-                                                    const typename Store<S>::T *__restrict__ src,
-                                                    typename Store<S>::T *__restrict__ dst, int x,
-                                                    int y, int z, bool near) {
-  using St = Store<S>;
-  const I self = ((I)z * g.ny + y) * g.nx + x;
-  float h[kQ];
-  if (near) {
-    const uint32_t bb = __ldg(&g.lmask[self]);
-    if (bb & 1u) return;  // solid node
-    pull19_mask<S, I>(g, src, x, y, z, bb, h);
-  } else {
-    pull19_mask<S, I>(g, src, x, y, z, 0u, h);  // constant mask: no selects
-  }
-  collide19<FORCING>(h, ph);
-  const I Vp = (I)g.Vp;
-#pragma unroll
-  for (int p = 0; p < kQ; ++p) St::store(dst + (I)p * Vp + self, h[p]);
-}
 
 // Six 256-thread blocks per SM (40 registers): the occupancy that measured
 // fastest for this kernel; it is HBM-bound and needs the loads of many warps

@@ -181,6 +181,7 @@ extern "C" int lbmd_lb_step_noalloc(const lbmd_params *p, const float *f_in, flo
   if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nz > 65535) return LBMD_EINVAL;
   if (!(p->tau > 0.5) || !(p->rho0 > 0)) return LBMD_EINVAL;
   if (p->storage != LBMD_STORE_F32 || p->n_beads != 0) return LBMD_EINVAL;
+  if (p->kT_fluid != 0.0) return LBMD_EUNSUPPORTED;  // no step counter for the noise
   if (p->forcing != LBMD_FORCING_PAPER && p->forcing != LBMD_FORCING_GUO) return LBMD_EINVAL;
   if (p->wall_x < -1 || p->wall_x >= p->nx) return LBMD_EINVAL;
   if (p->y_walls != 0 && p->y_walls != 1) return LBMD_EINVAL;

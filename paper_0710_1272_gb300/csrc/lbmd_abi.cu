@@ -114,9 +114,16 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     if ((e = cudaEventRecord(t[3], c->own)) != cudaSuccess) return e;
   }
   if (t[0] && (e = cudaEventRecord(t[0], c->own)) != cudaSuccess) return e;
-  if ((e = launch_lb_stream_collide(c->p.storage, c->geo, c->phys, A, B,
-                                    c->N > 0 ? nullptr : c->status, c->own)) != cudaSuccess)
+  if (c->phys.step) {
+    // thermal source: the kernel reads the step count, so a box without
+    // beads advances it in a separate launch afterwards
+    if ((e = launch_lb_stream_collide_fluct(c->p.storage, c->geo, c->phys, A, B, c->own)) != cudaSuccess)
+      return e;
+    if (c->N == 0 && (e = launch_bump_step(c->status, c->own)) != cudaSuccess) return e;
+  } else if ((e = launch_lb_stream_collide(c->p.storage, c->geo, c->phys, A, B,
+                                           c->N > 0 ? nullptr : c->status, c->own)) != cudaSuccess) {
     return e;
+  }
   if (t[1] && (e = cudaEventRecord(t[1], c->own)) != cudaSuccess) return e;
   if (c->N > 0) {
     if ((e = cudaEventRecord(c->ev_join, c->side)) != cudaSuccess) return e;

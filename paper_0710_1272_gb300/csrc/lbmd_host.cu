@@ -114,6 +114,8 @@ int validate(const lbmd_params *p) {
   if (p->solvent_free != 0 && p->solvent_free != 1)
     return fail(LBMD_EINVAL, "solvent_free must be 0 or 1");
   if (p->solvent_free && p->n_beads < 1) return fail(LBMD_EINVAL, "solvent_free needs n_beads >= 1");
+  if (!(p->kT_fluid >= 0) || !std::isfinite(p->kT_fluid))
+    return fail(LBMD_EINVAL, "kT_fluid must be >= 0");
   if (p->diag_every < 0 || p->diag_capacity < 0)
     return fail(LBMD_EINVAL, "diag_every and diag_capacity must be >= 0");
   if (p->diag_every > 0 && (p->n_beads < 1 || p->diag_capacity < 1))
@@ -287,6 +289,13 @@ cudaError_t init_instance(const lbmd_params &p, const Layout &L, char *ws, cudaS
   out.phys.rho0 = (float)p.rho0;
   for (int a = 0; a < 3; ++a) out.phys.g[a] = (float)p.body_force[a];
   out.phys.forcing = p.forcing;
+  out.phys.seed = p.seed;
+  out.phys.step = nullptr;
+  for (int k = 0; k < 15; ++k) out.phys.fl_amp[k] = 0.f;
+  if (p.kT_fluid > 0) {
+    fluct_amplitudes(p.kT_fluid, p.tau, out.phys.fl_amp);
+    out.phys.step = &out.status->step;
+  }
 
   // initial populations: (rho, u) staged in the second population buffer
   const float *drho = nullptr, *du = nullptr;

@@ -61,6 +61,10 @@ struct LbPhys {
   float rho0;
   float g[3];     // body force density
   int forcing;    // LBMD_FORCING_*
+  // thermal source F_p of Eq. 5 (used only by the fluctuating kernels):
+  float fl_amp[15];          // a_k = sqrt(3 kT (1 - (1 - omega)^2) / b_k), k = 4..18
+  unsigned long long seed;   // Philox key
+  const long long *step;     // LB steps completed (the noise counter); null: no noise
 };
 
 // Everything the MD kernel needs for one chain.
@@ -131,6 +135,15 @@ cudaError_t md_prepare();
 cudaError_t launch_lb_stream_collide(int storage, const LbGeom &g, const LbPhys &ph,
                                      const void *src, void *dst, DevStatus *bump,
                                      cudaStream_t s);
+// Stream-collide with the thermal source (ph.step != null); `bump` as above.
+cudaError_t launch_lb_stream_collide_fluct(int storage, const LbGeom &g, const LbPhys &ph,
+                                           const void *src, void *dst, cudaStream_t s);
+// Per-mode noise amplitudes a_k (k = 4..18) of the thermal source.
+void fluct_amplitudes(double kT, double tau, float amp[15]);
+// status->step += 1 (one thread): the step count of a box without beads when
+// the stream-collide reads it.
+cudaError_t launch_bump_step(DevStatus *status, cudaStream_t s);
+
 // Fill g.lmask from the solid bitfield (once, at set-up).
 cudaError_t launch_link_mask(const LbGeom &g, uint32_t *mask, cudaStream_t s);
 cudaError_t launch_init_populations(int storage, const LbGeom &g, float rho0,

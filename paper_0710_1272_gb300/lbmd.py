@@ -33,7 +33,7 @@ DEFAULTS = dict(
     bead_mass=1.0, gamma=0.1, kT=1e-4, lj_sigma=1.8, lj_eps=1.0,
     kappa_phi=0.0, f_drive=0.02, bond_len=1.2,
     shake_tol=1e-6, shake_max_iter=12, init_tg_amp=0.0, seed=0, hydrodynamics=1,
-    diag_every=0, diag_capacity=0,
+    diag_every=0, diag_capacity=0, kT_fluid=0.0,
 )
 IGNORED_KEYS = {"bonds"}  # oracle-only keys
 
@@ -51,7 +51,7 @@ class lbmd_params(C.Structure):
         ("bead_mass", C.c_double), ("gamma", C.c_double), ("kT", C.c_double),
         ("lj_sigma", C.c_double), ("lj_eps", C.c_double), ("kappa_phi", C.c_double),
         ("f_drive", C.c_double), ("bond_length", C.c_double), ("shake_tol", C.c_double),
-        ("init_tg_amp", C.c_double), ("seed", C.c_uint64),
+        ("init_tg_amp", C.c_double), ("kT_fluid", C.c_double), ("seed", C.c_uint64),
         ("bond_i", C.c_void_p), ("bond_j", C.c_void_p), ("bond_len", C.c_void_p),
         ("init_pos", C.c_void_p), ("init_vel", C.c_void_p),
         ("init_rho", C.c_void_p), ("init_u", C.c_void_p),
@@ -171,7 +171,7 @@ def make_params(p: dict, init_pos=None, init_vel=None, init_rho=None, init_u=Non
     cp.forcing = FORCING[p["forcing"]]
     cp.coupling = COUPLING[p["coupling"]]
     for k in ("tau", "rho0", "bead_mass", "gamma", "kT", "lj_sigma", "lj_eps", "kappa_phi",
-              "f_drive", "shake_tol", "init_tg_amp"):
+              "f_drive", "shake_tol", "init_tg_amp", "kT_fluid"):
         setattr(cp, k, float(p[k]))
     cp.bond_length = float(p["bond_len"])
     for a in range(3):
