@@ -54,6 +54,8 @@ def parse():
                     default="translocation")
     ap.add_argument("--box", type=int, default=256, help="edge of the periodic solvent box")
     ap.add_argument("--tau", type=float, default=1.0)
+    ap.add_argument("--kT-fluid", type=float, default=0.0,
+                    help="temperature of the fluid's thermal source (0: none)")
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the batched-ensemble leg")
     ap.add_argument("--ens-count", type=int, default=512)
@@ -76,10 +78,16 @@ def workload(seed: int, storage: str, args=None):
         p = si.paper_translocation(seed)
         p["tau"] = args.tau if args is not None else 1.0
     p["storage"] = storage
+    if args is not None and args.kT_fluid > 0:
+        p["kT_fluid"] = args.kT_fluid
     return p
 
 
 def workload_name(p) -> str:
+    if p.get("kT_fluid", 0) > 0:
+        q = dict(p)
+        q["kT_fluid"] = 0
+        return workload_name(q) + f", fluctuating (kT_fluid={p['kT_fluid']:g})"
     if p["n_beads"] > 0:
         return (f"translocation {p['nx']}x{p['ny']}x{p['nz']}, wall x={p['wall_x']}, "
                 f"{p['pore_d']}x{p['pore_d']} pore, N={p['n_beads']} beads, tau={p['tau']}")
@@ -180,7 +188,7 @@ def cpu_baseline(p, pos, seconds: float):
     import oracle
 
     cores = oracle.max_threads()
-    op = {k: v for k, v in p.items() if k not in ("storage", "init_tg_amp")}
+    op = {k: v for k, v in p.items() if k not in ("storage", "init_tg_amp", "diag_every", "diag_capacity")}
     init_u = (si.taylor_green_field(p["nx"], p["ny"], p["nz"], p["init_tg_amp"])
               if p.get("init_tg_amp") else None)
     sim = oracle.OracleSim(op, init_pos=pos, init_u=init_u)
@@ -352,7 +360,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": (2 * ((16 * N + 255) // 256 * 256) + 16 * N + 56) if N else 56,
                 "api": ("lbmd_step(1) + lbmd_read_beads(host) + lbmd_status per step" if N
                         else "lbmd_step(1) + lbmd_status per step")},
-        "gpu_launches": (4 if p["n_beads"] > 0 else 1) * args.steps,
+        "gpu_launches": (4 if p["n_beads"] > 0 else (2 if p.get("kT_fluid", 0) > 0 else 1)) * args.steps,
         "clocks": clocks,
         "status": st,
     }
