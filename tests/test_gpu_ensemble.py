@@ -301,3 +301,25 @@ def test_ensemble_diagnostics_match_single_box():
         for key in ("r_u", "r_t", "r_e", "s_h", "s_e", "kinetic"):
             assert np.allclose(d[key], ds[key], rtol=1e-4, atol=1e-7), (k, key)
         assert np.array_equal(d["n_trans"], ds["n_trans"])
+
+
+def test_many_small_realisations():
+    """1024 realisations (every MD group size from 1 to 64 beads, boxes of
+    8192 nodes): sampled members equal the single-box path after 20 steps."""
+    lb = _lb()
+    members, starts = [], []
+    for k in range(1024):
+        p = dict(si.BASE)
+        p.update(nx=32, ny=16, nz=16, wall_x=16, pore_d=3 if k % 2 else 5, n_beads=1 + (k * 7) % 40,
+                 seed=9000 + k, lj_eps=PAPER_EPS)
+        members.append(p)
+        starts.append(si.saw_chain(p, p["seed"]))
+    ens = lb.Ensemble(members, starts)
+    ens.step(20)
+    res = ens.results()
+    assert np.all(res["steps"][res["state"] == lb.RUNNING] == 20)
+    for k in (0, 1, 511, 777, 1023):
+        sim = lb.Simulation(members[k], init_pos=starts[k])
+        advance_like_member(sim, 20, lb.RUNNING)
+        assert rel_err(ens.populations(k), sim.populations().astype(np.float64)) < 1e-6, k
+        assert np.abs(ens.beads(k)[0] - sim.beads()[0]).max() < 1e-6, k

@@ -97,8 +97,7 @@ def test_storage_precision_variants(case):
     kept with 11 (fp16) or 8 (bf16) significant bits, i.e. an absolute error
     <= 2^-11 * 0.01 (fp16) or 2^-8 * 0.01 (bf16) per rounding; relative to the
     smallest population (1/36) that is <= 2e-4 and 1.2e-3 per step, and the
-    BGK relaxation keeps it from growing over the 10 steps checked.  Boxes with
-    even nx take the paired-node kernel, odd nx the per-node one."""
+    BGK relaxation keeps it from growing over the 10 steps checked."""
     p = LB_CASES[case]
     shape = (p["nz"], p["ny"], p["nx"])
     rho, u = si.random_flow(shape, seed=5 + case, u_max=0.03)
@@ -500,3 +499,40 @@ def test_thermal_source_not_in_ensembles():
     with pytest.raises(lb.LbmdError) as e:
         lb.Ensemble([p], [pos])
     assert e.value.code == lb.lbmd.LBMD_EUNSUPPORTED
+
+
+def test_box_beyond_32bit_population_offsets():
+    """The largest boxes (19 Vp >= 2^31) index the populations with 64-bit
+    offsets.  Checked on 512 x 512 x 456 (119.5 M nodes, 18 GB of FP32
+    populations) with properties that hold at any size: a 2-D Taylor-Green
+    vortex in a periodic box stays the same on every z-plane (bit for bit,
+    including the last plane, whose populations sit beyond 2^31 elements),
+    u_z stays 0 up to rounding (1e-6 |u|), mass is conserved, and the amplitude decays at
+    2 nu k^2, nu = (tau - 1/2)/3."""
+    torch = pytest.importorskip("torch")
+    lb = _gpu()
+    nx, ny, nz, tau, A = 512, 512, 456, 0.8, 0.01
+    assert 19 * nx * ny * nz > 2 ** 31
+    sim = lb.Simulation(dict(nx=nx, ny=ny, nz=nz, wall_x=-1, tau=tau, init_tg_amp=A))
+    k = 2 * np.pi / nx
+    xs = torch.arange(nx, device="cuda", dtype=torch.float64)
+    basis = torch.sin(k * xs)[None, :] * torch.cos(k * xs)[:, None]
+
+    def amplitude(ux):
+        return float((ux.double() * basis).sum() / (basis * basis).sum())
+
+    sim.step(100)
+    rho, u = sim.fields_device()
+    m0 = float(rho.double().sum())
+    a0 = amplitude(u[0, 0])
+    del rho, u
+    sim.step(200)
+    rho, u = sim.fields_device()
+    for z in (1, nz // 2, nz - 1):
+        assert torch.equal(u[:, z], u[:, 0]) and torch.equal(rho[z], rho[0]), z
+    # u_z = 0 by symmetry; float rounding of the +-z sums leaves ~1e-7 |u|
+    assert float(u[2].abs().max()) < 1e-6 * float(u[0].abs().max())
+    assert abs(float(rho.double().sum()) / m0 - 1) < 1e-6
+    a1 = amplitude(u[0, 0])
+    rate = -np.log(a1 / a0) / 200
+    assert rate / (2 * (tau - 0.5) / 3 * k * k) == pytest.approx(1.0, abs=0.02)
