@@ -323,3 +323,29 @@ def test_many_small_realisations():
         advance_like_member(sim, 20, lb.RUNNING)
         assert rel_err(ens.populations(k), sim.populations().astype(np.float64)) < 1e-6, k
         assert np.abs(ens.beads(k)[0] - sim.beads()[0]).max() < 1e-6, k
+
+
+def test_ensemble_forcing_and_coupling_variants():
+    """Options that only the single-box tests covered, now per realisation in
+    an ensemble: Guo forcing with a body force (shared), NGP coupling, bending
+    stiffness and y-walls (per realisation); every member against the oracle
+    after 5 steps (populations 2e-5, beads 1e-5)."""
+    lb = _lb()
+    specs = [
+        dict(nx=32, ny=16, nz=16, wall_x=16, pore_d=3, n_beads=12, seed=51, coupling="ngp"),
+        dict(nx=40, ny=18, nz=16, wall_x=20, pore_d=5, n_beads=20, seed=52, kappa_phi=0.5),
+        dict(nx=36, ny=17, nz=12, wall_x=18, pore_d=3, n_beads=9, seed=53, y_walls=1),
+    ]
+    members, starts = [], []
+    for sp in specs:
+        p = dict(si.BASE)
+        p.update(sp, lj_eps=PAPER_EPS, forcing="guo", body_force=(2e-5, 1e-6, 0.0))
+        members.append(p)
+        starts.append(si.saw_chain(p, p["seed"]))
+    ens = lb.Ensemble(members, starts)
+    ens.step(5)
+    for k, (p, pos) in enumerate(zip(members, starts)):
+        orc = oracle_of(p, pos)
+        orc.step(5)
+        assert rel_err(ens.populations(k), orc.populations()) < 2e-5, k
+        assert np.abs(ens.beads(k)[0] - orc.beads()[0]).max() < 1e-5, k
