@@ -17,7 +17,7 @@
  * interpolate u to the beads, run M MD substeps with u frozen, extrapolate the
  * bead forces to the grid, advance the populations.
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *  - D3Q19 weights 1/3, 1/18, 1/36 and c_s^2 = 1/3 (Sec. II cites the standard
  *    19-speed lattice without printing them).
  *  - The fluid receives the reaction -(F_drag + F_r) of the bead forces in
