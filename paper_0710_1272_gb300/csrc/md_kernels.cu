@@ -288,7 +288,6 @@ __device__ __forceinline__ F3 drive_force_at(const ChainArgs &a, float4 rh, floa
 
 // Bending (Eq. 3) and the Sec. III pulling force on bead i.
 __device__ F3 bend_drive_forces(const ChainArgs &a, int i, const float4 *s_rh, const float4 *s_rl) {
-  const LbGeom &g = a.geo;
   const int N = a.N;
   F3 F{0.f, 0.f, 0.f};
   if (a.kappa != 0.f && a.has_bonds) {
