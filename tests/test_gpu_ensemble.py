@@ -349,3 +349,28 @@ def test_ensemble_forcing_and_coupling_variants():
         orc.step(5)
         assert rel_err(ens.populations(k), orc.populations()) < 2e-5, k
         assert np.abs(ens.beads(k)[0] - orc.beads()[0]).max() < 1e-5, k
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16", 6e-4)])
+def test_bench_ensemble_full_size_sampled_against_oracle(storage, tol):
+    """The benchmark's ensemble at full size and in its launch configuration
+    (512 ragged realisations, 120.6 M nodes, autotuned stream-collide): after
+    two steps, sampled realisations of every chain length -- the N = 400 ones
+    in 144 x 80 x 80 boxes included -- against the oracle (FP32 1e-5, FP16 the
+    storage bound of the single-box tests)."""
+    lb = _lb()
+    members, starts = si.ragged_ensemble(512, seed=0)
+    ens = lb.Ensemble([dict(m, storage=storage) for m in members], starts)
+    ens.autotune(2)
+    ens.step(2)
+    seen = set()
+    for k, m in enumerate(members):
+        key = (m["n_beads"], m["pore_d"])
+        if key in seen or m["n_beads"] not in (20, 100, 400):
+            continue
+        seen.add(key)
+        orc = oracle_of(m, starts[k])
+        orc.step(2)
+        assert rel_err(ens.populations(k), orc.populations()) < tol, (k, key)
+        assert np.abs(ens.beads(k)[0] - orc.beads()[0]).max() < 1e-5, (k, key)
+    assert len(seen) >= 5
