@@ -360,22 +360,26 @@ int lbmd_ensemble_read_diagnostics(lbmd_ensemble *ens, int32_t member, lbmd_diag
                                    int32_t max_records, int32_t *n_records);
 
 /*
- * Launch shape of the ensemble stream-collide: tile height rows (4, 8 or 16),
- * register budget for warps resident warps per SM (32: 64 registers, or 48: 40
- * registers) and tiles taken per claim of the work counter (1 .. 64).
- * Default (8, 48, 2).  The CUDA graphs are re-captured at the next step.
+ * Launch shape of the ensemble stream-collide: tile height rows (4, 8 or 16
+ * rows of 32 consecutive nodes), register budget for warps resident warps per
+ * SM (32: 64 registers, or 48: 40 registers), tiles taken per claim of the
+ * work counter (1 .. 64) and cells per thread (1, or 2: the nodes at the same
+ * (x, y) on two consecutive z-planes, with warps = 32 and rows 4 or 8 only).
+ * Default (8, 48, 2, 1).  The CUDA graphs are re-captured at the next step.
  */
-int lbmd_ensemble_set_tuning(lbmd_ensemble *ens, int32_t rows, int32_t warps, int32_t claim);
-int lbmd_ensemble_get_tuning(lbmd_ensemble *ens, int32_t *rows, int32_t *warps, int32_t *claim);
+int lbmd_ensemble_set_tuning(lbmd_ensemble *ens, int32_t rows, int32_t warps, int32_t claim,
+                             int32_t cells_per_thread);
+int lbmd_ensemble_get_tuning(lbmd_ensemble *ens, int32_t *rows, int32_t *warps, int32_t *claim,
+                             int32_t *cells_per_thread);
 
 /*
  * Autotuner: times the stream-collide alone, `trials` launches per shape, for
- * every rows in {4, 8, 16} x warps in {32, 48} x claim in {1, 2, 4, 8}, on the
- * live realisations' current populations, and keeps the fastest shape.  The
- * trial launches write exactly what the next step's stream-collide writes
- * (from the same input), so the simulation is unchanged.  *best_ms (may be
- * NULL) receives the fastest average launch time (0 for a solvent-free
- * ensemble, which has no stream-collide).  Synchronises.
+ * every shape above (cells per thread 1 or 2, rows, warps, claim in
+ * {1, 2, 4, 8}) on the live realisations' current populations, and keeps the
+ * fastest.  The trial launches write exactly what the next step's
+ * stream-collide writes (from the same input), so the simulation is
+ * unchanged.  *best_ms (may be NULL) receives the fastest average launch time
+ * (0 for a solvent-free ensemble, which has no stream-collide).  Synchronises.
  */
 int lbmd_ensemble_autotune(lbmd_ensemble *ens, int32_t trials, double *best_ms);
 

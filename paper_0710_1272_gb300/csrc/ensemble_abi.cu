@@ -124,7 +124,7 @@ struct lbmd_ensemble {
   int2 *d_beads;
   long long *d_cap;
   float *stage;
-  int rows, warps, claim, grid, sms;
+  int rows, warps, claim, cpt, grid, sms;
   long long G;        // ensemble steps enqueued so far
   long long cap;
   int tiles_live;     // realisations in the current tile list
@@ -179,8 +179,9 @@ cudaError_t upload_tiles(lbmd_ensemble *e, const std::vector<int> &live) {
     ++n_live;
     const lbmd_params &p = e->p[m];
     const int plane = p.nx * p.ny, ts = 32 * e->rows;
-    for (int z = 0; z < p.nz; ++z)
-      for (int r0 = 0; r0 < plane; r0 += ts) e->htiles.push_back(EnsTile{m, z, r0, 0});
+    for (int z0 = 0; z0 < p.nz; z0 += e->cpt)
+      for (int r0 = 0; r0 < plane; r0 += ts)
+        e->htiles.push_back(EnsTile{m, z0, r0, std::min(e->cpt, p.nz - z0)});
   }
   const int n = (int)e->htiles.size();
   cudaError_t err;
@@ -274,7 +275,7 @@ cudaError_t enqueue_ens_step(lbmd_ensemble *e, int cur) {
   }
   if (t[1] && (err = cudaEventRecord(t[1], e->own)) != cudaSuccess) return err;
   if (!e->solvent_free &&
-      (err = launch_ens_stream_collide(e->storage, e->forcing, e->rows, e->warps, e->claim, e->grid,
+      (err = launch_ens_stream_collide(e->storage, e->forcing, e->rows, e->warps, e->cpt, e->claim, e->grid,
                                        e->d_lbd, e->d_tiles, e->d_n_tiles, e->d_counter, live, cur,
                                        e->own)) != cudaSuccess)
     return err;
@@ -335,8 +336,8 @@ int enqueue_steps(lbmd_ensemble *e, int64_t n) {
 }
 
 int set_grid(lbmd_ensemble *e) {
-  const int per_sm = ens_lb_blocks_per_sm(e->storage, e->forcing, e->rows, e->warps);
-  if (per_sm < 1) return fail(LBMD_ECUDA, "ensemble stream-collide does not fit on an SM");
+  const int per_sm = ens_lb_blocks_per_sm(e->storage, e->forcing, e->rows, e->warps, e->cpt);
+  if (per_sm < 1) return fail(LBMD_EINVAL, "no ensemble stream-collide of this launch shape");
   e->grid = e->sms * per_sm;
   return LBMD_OK;
 }
@@ -412,6 +413,7 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
   e->rows = 8;
   e->warps = 48;
   e->claim = 2;
+  e->cpt = 1;
   e->cap = LLONG_MAX;
 
   auto bail = [&](cudaError_t err, const char *what) {
@@ -652,17 +654,23 @@ int lbmd_ensemble_read_diagnostics(lbmd_ensemble *e, int32_t member, lbmd_diag *
                           max_records, n_records, e->own);
 }
 
-int lbmd_ensemble_set_tuning(lbmd_ensemble *e, int32_t rows, int32_t warps, int32_t claim) {
+int lbmd_ensemble_set_tuning(lbmd_ensemble *e, int32_t rows, int32_t warps, int32_t claim,
+                             int32_t cells_per_thread) {
   int rc = check_ens(e);
   if (rc) return rc;
   if (rows != 4 && rows != 8 && rows != 16) return fail(LBMD_EINVAL, "rows must be 4, 8 or 16");
   if (warps != 32 && warps != 48) return fail(LBMD_EINVAL, "warps must be 32 or 48");
   if (claim < 1 || claim > 64) return fail(LBMD_EINVAL, "claim must be in [1, 64]");
+  if (cells_per_thread != 1 && cells_per_thread != 2)
+    return fail(LBMD_EINVAL, "cells_per_thread must be 1 or 2");
+  if (cells_per_thread == 2 && (warps != 32 || rows == 16))
+    return fail(LBMD_EINVAL, "two cells per thread need warps = 32 and rows 4 or 8");
   EK(e, cudaStreamSynchronize(e->own));
-  const bool retile = rows != e->rows;
+  const bool retile = rows != e->rows || cells_per_thread != e->cpt;
   e->rows = rows;
   e->warps = warps;
   e->claim = claim;
+  e->cpt = cells_per_thread;
   if ((rc = set_grid(e))) return rc;
   drop_graphs(e);
   if (retile) {
@@ -673,12 +681,14 @@ int lbmd_ensemble_set_tuning(lbmd_ensemble *e, int32_t rows, int32_t warps, int3
   return LBMD_OK;
 }
 
-int lbmd_ensemble_get_tuning(lbmd_ensemble *e, int32_t *rows, int32_t *warps, int32_t *claim) {
+int lbmd_ensemble_get_tuning(lbmd_ensemble *e, int32_t *rows, int32_t *warps, int32_t *claim,
+                             int32_t *cells_per_thread) {
   int rc = check_ens(e);
   if (rc) return rc;
   if (rows) *rows = e->rows;
   if (warps) *warps = e->warps;
   if (claim) *claim = e->claim;
+  if (cells_per_thread) *cells_per_thread = e->cpt;
   return LBMD_OK;
 }
 
@@ -701,15 +711,17 @@ int lbmd_ensemble_autotune(lbmd_ensemble *e, int32_t trials, double *best_ms) {
   const int cur = (int)(e->G & 1);
   const int *live = e->d_live + cur * e->count;
   double best = 1e30;
-  int br = e->rows, bw = e->warps, bc = e->claim;
+  int br = e->rows, bw = e->warps, bc = e->claim, bz = e->cpt;
   cudaError_t err = cudaSuccess;
   std::vector<int> hl;
   if ((err = read_live(e, hl)) != cudaSuccess) goto done;
+  for (int cpt : {1, 2})
   for (int rows : {4, 8, 16}) {
     e->rows = rows;
+    e->cpt = cpt;
     if ((err = upload_tiles(e, hl)) != cudaSuccess) goto done;
     for (int warps : {32, 48}) {
-      const int per_sm = ens_lb_blocks_per_sm(e->storage, e->forcing, rows, warps);
+      const int per_sm = ens_lb_blocks_per_sm(e->storage, e->forcing, rows, warps, cpt);
       if (per_sm < 1) continue;
       for (int claim : {1, 2, 4, 8}) {
         // one untimed launch, then `trials` timed ones; the counter is reset
@@ -717,7 +729,7 @@ int lbmd_ensemble_autotune(lbmd_ensemble *e, int32_t trials, double *best_ms) {
         for (int k = 0; k <= trials; ++k) {
           if ((err = cudaMemsetAsync(e->d_counter, 0, sizeof(int), e->own)) != cudaSuccess) goto done;
           if (k == 1 && (err = cudaEventRecord(t0, e->own)) != cudaSuccess) goto done;
-          if ((err = launch_ens_stream_collide(e->storage, e->forcing, rows, warps, claim, e->sms * per_sm,
+          if ((err = launch_ens_stream_collide(e->storage, e->forcing, rows, warps, cpt, claim, e->sms * per_sm,
                                                e->d_lbd, e->d_tiles, e->d_n_tiles, e->d_counter, live,
                                                cur, e->own)) != cudaSuccess)
             goto done;
@@ -733,6 +745,7 @@ int lbmd_ensemble_autotune(lbmd_ensemble *e, int32_t trials, double *best_ms) {
           br = rows;
           bw = warps;
           bc = claim;
+          bz = cpt;
         }
       }
     }
@@ -744,6 +757,7 @@ done:
   e->rows = br;
   e->warps = bw;
   e->claim = bc;
+  e->cpt = bz;
   if ((rc = set_grid(e))) return rc;
   drop_graphs(e);
   EK(e, upload_tiles(e, hl));

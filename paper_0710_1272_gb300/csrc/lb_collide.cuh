@@ -148,4 +148,38 @@ __device__ __forceinline__ void stream_collide_node(const LbGeom &g, const LbPhy
 }
 
 
+// Nodes (x, y, z) and (x, y, z + 1) of one box (z + 1 < nz), with all 38
+// loads issued before either collision.  near: take the bounce-back checks
+// for both.
+template <int S, int FORCING>
+__device__ __forceinline__ void stream_collide_node2(const LbGeom &g, const LbPhys &ph,
+                                                     const typename Store<S>::T *__restrict__ src,
+                                                     typename Store<S>::T *__restrict__ dst, int x,
+                                                     int y, int z, bool near) {
+  using St = Store<S>;
+  const int self_a = (z * g.ny + y) * g.nx + x, self_b = self_a + g.nx * g.ny;
+  float ha[kQ], hb[kQ];
+  uint32_t ma = 0u, mb = 0u;
+  if (near) {
+    ma = __ldg(&g.lmask[self_a]);
+    mb = __ldg(&g.lmask[self_b]);
+    pull19_mask<S, int>(g, src, x, y, z, ma, ha);
+    pull19_mask<S, int>(g, src, x, y, z + 1, mb, hb);
+  } else {
+    pull19_mask<S, int>(g, src, x, y, z, 0u, ha);  // constant masks: no selects
+    pull19_mask<S, int>(g, src, x, y, z + 1, 0u, hb);
+  }
+  const int Vp = (int)g.Vp;
+  if (!(ma & 1u)) {  // a solid node is pulled but not written
+    collide19<FORCING>(ha, ph);
+#pragma unroll
+    for (int p = 0; p < kQ; ++p) St::store(dst + p * Vp + self_a, ha[p]);
+  }
+  if (!(mb & 1u)) {
+    collide19<FORCING>(hb, ph);
+#pragma unroll
+    for (int p = 0; p < kQ; ++p) St::store(dst + p * Vp + self_b, hb[p]);
+  }
+}
+
 }  // namespace lbmd

@@ -168,12 +168,14 @@ cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, cons
 // gather).  Every realisation must have 19 Vp < 2^31 (32-bit offsets) and
 // nx * ny < 2^22 (float row division).
 // forcing: LBMD_FORCING_* or kForcingNone (every realisation has g = 0).
-cudaError_t launch_ens_stream_collide(int storage, int forcing, int rows, int warps, int claim,
-                                      int grid, const EnsLb *lbd, const EnsTile *tiles,
+// cpt: cells per thread, 1 or 2 (two consecutive z-planes; warps 32 and rows
+// 4 or 8 only -- other shapes are cudaErrorInvalidValue).
+cudaError_t launch_ens_stream_collide(int storage, int forcing, int rows, int warps, int cpt,
+                                      int claim, int grid, const EnsLb *lbd, const EnsTile *tiles,
                                       const int *n_tiles, int *counter, const int *live, int cur,
                                       cudaStream_t s);
-// Blocks of that kernel that fit on one SM.
-int ens_lb_blocks_per_sm(int storage, int forcing, int rows, int warps);
+// Blocks of that kernel that fit on one SM (0: no such shape).
+int ens_lb_blocks_per_sm(int storage, int forcing, int rows, int warps, int cpt);
 // Gather for every (realisation, bead) of `beads` (padded entries have m < 0).
 cudaError_t launch_ens_gather(int storage, const EnsMember *mem, const int2 *beads, int nb,
                               const int *live, int cur, int *counter, cudaStream_t s);

@@ -125,8 +125,8 @@ def load(build_if_missing: bool = True):
     L.lbmd_ensemble_live.argtypes = [P, PI32]
     L.lbmd_ensemble_read_beads.argtypes = [P, C.c_int32, P, P, C.c_int]
     L.lbmd_ensemble_read_populations.argtypes = [P, C.c_int32, P, C.c_int]
-    L.lbmd_ensemble_set_tuning.argtypes = [P, C.c_int32, C.c_int32, C.c_int32]
-    L.lbmd_ensemble_get_tuning.argtypes = [P, PI32, PI32, PI32]
+    L.lbmd_ensemble_set_tuning.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+    L.lbmd_ensemble_get_tuning.argtypes = [P, PI32, PI32, PI32, PI32]
     L.lbmd_ensemble_autotune.argtypes = [P, C.c_int32, PD]
     L.lbmd_ensemble_set_kernel_timing.argtypes = [P, C.c_int]
     L.lbmd_ensemble_kernel_times.argtypes = [P, PD, PD, PI64]
@@ -357,16 +357,16 @@ def lbmd_ensemble_read_populations(ens, member: int, f_ptr, dst_is_device: int) 
            "lbmd_ensemble_read_populations")
 
 
-def lbmd_ensemble_set_tuning(ens, rows: int, warps: int, claim: int) -> None:
-    _check(load().lbmd_ensemble_set_tuning(ens, int(rows), int(warps), int(claim)),
+def lbmd_ensemble_set_tuning(ens, rows: int, warps: int, claim: int, cells_per_thread: int = 1) -> None:
+    _check(load().lbmd_ensemble_set_tuning(ens, int(rows), int(warps), int(claim), int(cells_per_thread)),
            "lbmd_ensemble_set_tuning")
 
 
 def lbmd_ensemble_get_tuning(ens) -> dict:
-    r, w, c = C.c_int32(), C.c_int32(), C.c_int32()
-    _check(load().lbmd_ensemble_get_tuning(ens, C.byref(r), C.byref(w), C.byref(c)),
+    r, w, c, z = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().lbmd_ensemble_get_tuning(ens, C.byref(r), C.byref(w), C.byref(c), C.byref(z)),
            "lbmd_ensemble_get_tuning")
-    return dict(rows=r.value, warps=w.value, claim=c.value)
+    return dict(rows=r.value, warps=w.value, claim=c.value, cells_per_thread=z.value)
 
 
 def lbmd_ensemble_autotune(ens, trials: int = 3) -> float:
@@ -558,8 +558,8 @@ class Ensemble:
         lbmd_ensemble_read_populations(self.ens, member, f.ctypes.data, 0)
         return f
 
-    def set_tuning(self, rows: int, warps: int, claim: int) -> None:
-        lbmd_ensemble_set_tuning(self.ens, rows, warps, claim)
+    def set_tuning(self, rows: int, warps: int, claim: int, cells_per_thread: int = 1) -> None:
+        lbmd_ensemble_set_tuning(self.ens, rows, warps, claim, cells_per_thread)
 
     def tuning(self) -> dict:
         return lbmd_ensemble_get_tuning(self.ens)

@@ -190,6 +190,7 @@ def test_ensemble_autotune_leaves_the_state_unchanged():
     assert ms > 0
     t = a.tuning()
     assert t["rows"] in (4, 8, 16) and t["warps"] in (32, 48) and 1 <= t["claim"] <= 8
+    assert t["cells_per_thread"] in (1, 2)
     a.step(6)
     b.step(11)
     for k in range(len(members)):
@@ -197,13 +198,16 @@ def test_ensemble_autotune_leaves_the_state_unchanged():
         assert np.abs(a.beads(k)[0] - b.beads(k)[0]).max() < 1e-6, k
 
 
-@pytest.mark.parametrize("rows,warps,claim", [(4, 32, 1), (16, 48, 8), (8, 32, 3)])
-def test_ensemble_tile_shapes_agree(rows, warps, claim):
+@pytest.mark.parametrize("rows,warps,claim,cpt", [(4, 32, 1, 1), (16, 48, 8, 1), (8, 32, 3, 1),
+                                                  (4, 32, 2, 2), (8, 32, 5, 2)])
+def test_ensemble_tile_shapes_agree(rows, warps, claim, cpt):
+    """Every launch shape updates every node once; two cells per thread leave a
+    single-plane tile on the boxes with odd nz (13 and 17)."""
     lb = _lb()
     members, starts = ragged_members()
     a = lb.Ensemble(members, starts)
     b = lb.Ensemble(members, starts)
-    a.set_tuning(rows, warps, claim)
+    a.set_tuning(rows, warps, claim, cpt)
     a.step(7)
     b.step(7)
     for k in range(len(members)):
