@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--streaming", choices=["pull", "aa"], default="pull",
+                    help="two-buffer pull streaming or the one-buffer in-place (AA) pattern")
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -65,6 +67,10 @@ def parse():
     return ap.parse_args()
 
 
+# parameters of the GPU library that the oracle does not take
+GPU_ONLY_KEYS = ("storage", "init_tg_amp", "diag_every", "diag_capacity", "streaming")
+
+
 def workload(seed: int, storage: str, args=None):
     """Parameters of the timed workload (all inputs seeded and synthetic)."""
     kind = args.workload if args is not None else "translocation"
@@ -78,6 +84,8 @@ def workload(seed: int, storage: str, args=None):
         p = si.paper_translocation(seed)
         p["tau"] = args.tau if args is not None else 1.0
     p["storage"] = storage
+    if args is not None:
+        p["streaming"] = args.streaming
     if args is not None and args.kT_fluid > 0:
         p["kT_fluid"] = args.kT_fluid
     return p
@@ -188,7 +196,7 @@ def cpu_baseline(p, pos, seconds: float):
     import oracle
 
     cores = oracle.max_threads()
-    op = {k: v for k, v in p.items() if k not in ("storage", "init_tg_amp", "diag_every", "diag_capacity")}
+    op = {k: v for k, v in p.items() if k not in GPU_ONLY_KEYS}
     init_u = (si.taylor_green_field(p["nx"], p["ny"], p["nz"], p["init_tg_amp"])
               if p.get("init_tg_amp") else None)
     sim = oracle.OracleSim(op, init_pos=pos, init_u=init_u)
@@ -214,7 +222,7 @@ def run_reference(args):
     pos = si.saw_chain(p, 0) if p["n_beads"] > 0 else None
     import oracle
 
-    op = {k: v for k, v in p.items() if k not in ("storage", "init_tg_amp")}
+    op = {k: v for k, v in p.items() if k not in GPU_ONLY_KEYS}
     init_u = (si.taylor_green_field(p["nx"], p["ny"], p["nz"], p["init_tg_amp"])
               if p.get("init_tg_amp") else None)
     sim = oracle.OracleSim(op, init_pos=pos, init_u=init_u)
@@ -324,15 +332,19 @@ def run_ours(args):
     bytes_per_launch = BYTES_PER_NODE[args.storage] * fluid
     lb_avg_s = lb_ms / 1e3 / max(lb_n, 1)
     achieved = bytes_per_launch / lb_avg_s / 1e9
+    kernel = "k_aa_stream_collide" if args.streaming == "aa" else "k_stream_collide"
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "lb_stream_collide_traffic.json")
     if os.path.exists(tpath):
         try:
             with open(tpath) as f:
-                tj = json.load(f)
-            if tj.get("storage") == args.storage and tj.get("kernel_rev") == kernel_rev():
-                traffic = tj["bytes_per_launch"]
-        except (OSError, ValueError, KeyError):
+                records = json.load(f)["records"]
+            rev = kernel_rev(kernel)
+            for tj in records:
+                if (tj["kernel"], tj["storage"], tj["workload"], tj["kernel_rev"]) == \
+                        (kernel, args.storage, workload_name(p), rev):
+                    traffic = tj["bytes_per_launch"]
+        except (OSError, ValueError, KeyError, TypeError):
             traffic = None
     clocks = clk.summary()
     line = {
@@ -341,6 +353,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.storage, "data": "synthetic",
         "config": {"workload": workload_name(p), "storage": args.storage,
+                   "streaming": args.streaming,
                    "seed": shard_seed(0, rank), "parallelism":
                    "independent realisation per GPU" if world > 1 else "1 GPU",
                    "l2": (f"no flush: populations {2 * BYTES_PER_NODE[args.storage] * V / 2 / 1e6:.1f} "
@@ -350,7 +363,7 @@ def run_ours(args):
         "value_direct_launch": world * V * args.steps / (ms_direct / 1e3) / 1e6,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_stream_collide", "peak_source": f"{peak_kind} hbm_gbs",
+                     "kernel": kernel, "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": lb_avg_s * 1e3, "launches_timed": lb_n},
         "e2e": {"value": world * V * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
@@ -470,13 +483,21 @@ def ensemble_leg(args, lb, torch, dist, rank, world):
     return out
 
 
-def kernel_rev() -> str:
-    """Hash of the stream-collide sources: a stored DRAM-traffic figure is only
-    reported while the kernel it was measured on is unchanged."""
+KERNEL_SOURCES = {
+    "k_stream_collide": ("lb_kernels.cu", "lb_collide.cuh", "lb_pull.cuh", "lbmd_common.cuh",
+                         "lbmd_internal.h"),
+    "k_aa_stream_collide": ("lb_aa.cu", "lb_aa.cuh", "lb_collide.cuh", "lb_pull.cuh",
+                            "lbmd_common.cuh", "lbmd_internal.h"),
+}
+
+
+def kernel_rev(kernel: str = "k_stream_collide") -> str:
+    """Hash of a stream-collide kernel's sources: a stored DRAM-traffic figure
+    is only reported while the kernel it was measured on is unchanged."""
     import hashlib
 
     h = hashlib.sha256()
-    for name in ("lb_kernels.cu", "lb_pull.cuh", "lbmd_common.cuh"):
+    for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_0710_1272_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -64,6 +64,8 @@ extern "C" {
 #define LBMD_FORCING_GUO 1   /* Guo second-order forcing for the body force  */
 #define LBMD_COUPLING_TRILINEAR 0 /* 8-node trilinear gather / spread        */
 #define LBMD_COUPLING_NGP 1       /* nearest grid point (the paper's choice) */
+#define LBMD_STREAM_PULL 0 /* two population buffers, pull streaming (A -> B) */
+#define LBMD_STREAM_AA 1   /* one buffer, in-place AA-pattern streaming      */
 
 /* Largest chain one context accepts (one GPU thread block per chain). */
 #define LBMD_MAX_BEADS 1024
@@ -98,6 +100,13 @@ typedef struct lbmd_params {
                                   at the end of every diag_every-th step;
                                   0: never                                  */
   int32_t diag_capacity;       /* records kept (later ones are dropped)     */
+  int32_t streaming;           /* LBMD_STREAM_*: how Eq. 5's free streaming
+                                  moves the populations.  PULL keeps two
+                                  buffers; AA (in-place, Bailey et al. 2009)
+                                  keeps one, halving the population memory,
+                                  with the same results and the same bytes
+                                  moved per node update.  Single-box contexts
+                                  only.                                     */
   double tau;                  /* BGK relaxation time, nu = (tau - 1/2)/3   */
   double rho0;                 /* reference density (paper: 1)              */
   double body_force[3];        /* uniform force density g                   */
@@ -144,7 +153,8 @@ typedef struct lbmd_diag {
 
 /*
  * Bytes of device workspace lbmd_create needs for these parameters (two
- * population buffers, the solid bitfield, bead state and read-out staging).
+ * population buffers -- one with LBMD_STREAM_AA --, the solid bitfield and
+ * link masks, bead state and read-out staging).
  * Validates the parameters; no CUDA call, callable without a GPU.
  * Errors: LBMD_EINVAL (bad parameter, message in lbmd_last_message).
  */
@@ -305,8 +315,8 @@ typedef struct lbmd_ensemble lbmd_ensemble;
 /*
  * Workspace bytes for `count` realisations members[0 .. count-1].  Each member
  * is validated as by lbmd_workspace_size and must further have
- * n_beads >= 1, 19 * nx*ny*nz < 2^31, nx*ny < 2^22 and kT_fluid = 0; all
- * members must share storage, forcing and solvent_free (LBMD_EUNSUPPORTED
+ * n_beads >= 1, 19 * nx*ny*nz < 2^31, nx*ny < 2^22, kT_fluid = 0 and
+ * streaming = LBMD_STREAM_PULL; all members must share storage, forcing and solvent_free (LBMD_EUNSUPPORTED
  * otherwise).  count must be >= 1.
  */
 int lbmd_ensemble_workspace_size(const lbmd_params *members, int32_t count, size_t *bytes);

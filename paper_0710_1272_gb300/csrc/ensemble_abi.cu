@@ -56,6 +56,8 @@ int validate_members(const lbmd_params *m, int32_t count) {
       return fail(LBMD_EUNSUPPORTED, "member %d: box too large for 32-bit population offsets", k);
     if (m[k].kT_fluid != 0.0)
       return fail(LBMD_EUNSUPPORTED, "member %d: the thermal source is single-box only", k);
+    if (m[k].streaming != LBMD_STREAM_PULL)
+      return fail(LBMD_EUNSUPPORTED, "member %d: in-place streaming is single-box only", k);
     if ((long long)m[k].nx * m[k].ny >= (1LL << 22))
       return fail(LBMD_EUNSUPPORTED, "member %d: nx * ny must be < 2^22", k);
     if (m[k].storage != m[0].storage || m[k].forcing != m[0].forcing ||
@@ -452,6 +454,7 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
     memset(&M, 0, sizeof(M));
     M.a = e->inst[m].chain;
     M.a.f = nullptr;
+    M.a.f_mode = kPopPull;
     M.ph = e->inst[m].phys;
     M.pop[0] = e->inst[m].pop[0];
     M.pop[1] = e->inst[m].pop[1];
@@ -624,7 +627,7 @@ int lbmd_ensemble_read_populations(lbmd_ensemble *e, int32_t member, float *f, i
   const float rho0 = (float)e->p[member].rho0;
   const void *src = in.pop[st.out_buf & 1];
   if (dst_is_device) {
-    EK(e, launch_read_pulled(e->storage, g, rho0, src, 0, g.nz, f, g.V, e->own));
+    EK(e, launch_read_pulled(e->storage, g, rho0, src, kPopPull, 0, g.nz, f, g.V, e->own));
     EK(e, cudaStreamSynchronize(e->own));
     return LBMD_OK;
   }
@@ -633,7 +636,7 @@ int lbmd_ensemble_read_populations(lbmd_ensemble *e, int32_t member, float *f, i
   for (long long z0 = 0; z0 < g.nz; z0 += nzc_max) {
     const long long nzc = std::min(nzc_max, (long long)g.nz - z0);
     const long long cells = nzc * plane;
-    EK(e, launch_read_pulled(e->storage, g, rho0, src, z0, nzc, e->stage, cells, e->own));
+    EK(e, launch_read_pulled(e->storage, g, rho0, src, kPopPull, z0, nzc, e->stage, cells, e->own));
     for (int q = 0; q < 19; ++q)
       EK(e, cudaMemcpyAsync(f + q * g.V + z0 * plane, e->stage + q * cells, cells * 4,
                             cudaMemcpyDeviceToHost, e->own));

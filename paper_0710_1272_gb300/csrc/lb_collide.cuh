@@ -77,6 +77,10 @@ __device__ __forceinline__ void thermal_source(const LbPhys &ph, uint32_t node, 
 // Opposite directions p, opp(p) = p + 1 (odd p) share c.u up to the sign, so
 // heq splits into the even part w_p [(rho - rho0) - 3/2 rho u.u + 9/2 rho (c.u)^2]
 // and the odd part +-3 w_p rho c.u, computed once per pair.
+// Every multiply-add is written out as fmaf, and every product that is added
+// afterwards as __fmul_rn / __fadd_rn, so the compiler cannot contract
+// differently in different kernels: the pull, in-place and ensemble
+// stream-collides round identically.
 template <int FORCING, bool FLUCT = false>
 __device__ __forceinline__ void collide19(float h[kQ], const LbPhys &ph, uint32_t node = 0) {
   float drho, jx, jy, jz;
@@ -85,40 +89,44 @@ __device__ __forceinline__ void collide19(float h[kQ], const LbPhys &ph, uint32_
   const float inv = __frcp_rn(rho);  // correctly rounded, as 1.0f / rho
   float ux, uy, uz;
   if (FORCING == LBMD_FORCING_GUO) {
-    ux = (jx + 0.5f * ph.g[0]) * inv;
-    uy = (jy + 0.5f * ph.g[1]) * inv;
-    uz = (jz + 0.5f * ph.g[2]) * inv;
+    ux = __fmul_rn(fmaf(0.5f, ph.g[0], jx), inv);
+    uy = __fmul_rn(fmaf(0.5f, ph.g[1], jy), inv);
+    uz = __fmul_rn(fmaf(0.5f, ph.g[2], jz), inv);
   } else {
-    ux = jx * inv;
-    uy = jy * inv;
-    uz = jz * inv;
+    ux = __fmul_rn(jx, inv);
+    uy = __fmul_rn(jy, inv);
+    uz = __fmul_rn(jz, inv);
   }
   const float om = ph.omega, om1 = 1.0f - om;
-  const float A = drho - 1.5f * rho * (ux * ux + uy * uy + uz * uz);
-  const float r3 = 3.0f * rho, r45 = 4.5f * rho;
-  const float gu = ph.g[0] * ux + ph.g[1] * uy + ph.g[2] * uz;
-  const float kguo = 1.0f - 0.5f * om;
-  auto source = [&](int p, float cu) {
-    const float cg = cx(p) * ph.g[0] + cy(p) * ph.g[1] + cz(p) * ph.g[2];
-    if (FORCING == LBMD_FORCING_GUO) return kguo * wq(p) * (3.0f * (cg - gu) + 9.0f * cu * cg);
-    if (FORCING == LBMD_FORCING_PAPER) return 3.0f * wq(p) * cg;
-    return 0.f;
+  const float usq = fmaf(uz, uz, fmaf(uy, uy, __fmul_rn(ux, ux)));
+  const float A = fmaf(-__fmul_rn(1.5f, rho), usq, drho);
+  const float r3 = __fmul_rn(3.0f, rho), r45 = __fmul_rn(4.5f, rho);
+  const float gu = fmaf(ph.g[2], uz, fmaf(ph.g[1], uy, __fmul_rn(ph.g[0], ux)));
+  const float kguo = fmaf(-0.5f, om, 1.0f);
+  // h*_p from the relaxed part, plus the source S_p (c_p . u = cu)
+  auto add_source = [&](int p, float cu, float v) {
+    const float cg = cx(p) * ph.g[0] + cy(p) * ph.g[1] + cz(p) * ph.g[2];  // +-g_a sums: exact order
+    if (FORCING == LBMD_FORCING_GUO) {
+      const float t = fmaf(__fmul_rn(9.0f, cu), cg, __fmul_rn(3.0f, cg - gu));
+      return __fadd_rn(v, __fmul_rn(__fmul_rn(kguo, wq(p)), t));
+    }
+    if (FORCING == LBMD_FORCING_PAPER) return __fadd_rn(v, __fmul_rn(3.0f * wq(p), cg));
+    return v;
   };
   float xi[kQ];
   if (FLUCT) thermal_source(ph, node, rho, xi);
-  h[0] = om1 * h[0] + (om * wq(0)) * A + source(0, 0.f);
-  if (FLUCT) h[0] += xi[0];
+  h[0] = add_source(0, 0.f, fmaf(__fmul_rn(om, wq(0)), A, __fmul_rn(om1, h[0])));
+  if (FLUCT) h[0] = __fadd_rn(h[0], xi[0]);
 #pragma unroll
   for (int p = 1; p < kQ; p += 2) {
-    const float cu = cx(p) * ux + cy(p) * uy + cz(p) * uz;  // c_opp(p) . u = -cu
-    const float even = fmaf(r45 * cu, cu, A);
-    const float odd = r3 * cu;
-    const float ow = om * wq(p);
-    h[p] = fmaf(ow, even + odd, om1 * h[p]) + source(p, cu);
-    h[p + 1] = fmaf(ow, even - odd, om1 * h[p + 1]) + source(p + 1, -cu);
+    const float cu = cx(p) * ux + cy(p) * uy + cz(p) * uz;  // +-u_a sums; c_opp(p) . u = -cu
+    const float even = fmaf(__fmul_rn(r45, cu), cu, A);
+    const float ow = __fmul_rn(om, wq(p));
+    h[p] = add_source(p, cu, fmaf(ow, fmaf(r3, cu, even), __fmul_rn(om1, h[p])));
+    h[p + 1] = add_source(p + 1, -cu, fmaf(ow, fmaf(-r3, cu, even), __fmul_rn(om1, h[p + 1])));
     if (FLUCT) {
-      h[p] += xi[p];
-      h[p + 1] += xi[p + 1];
+      h[p] = __fadd_rn(h[p], xi[p]);
+      h[p + 1] = __fadd_rn(h[p + 1], xi[p + 1]);
     }
   }
 }

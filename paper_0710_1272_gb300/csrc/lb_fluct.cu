@@ -1,9 +1,10 @@
 // lb_fluct.cu -- the stream-collide with the thermal source F_p of Eq. 5
 // (fluctuating LB), in its own translation unit: the same node update as
-// k_stream_collide plus fifteen Philox normals per node.
+// k_stream_collide (pull) or k_aa_stream_collide (in place) plus fifteen
+// Philox normals per node.
 #include <cmath>
 
-#include "lb_collide.cuh"
+#include "lb_aa.cuh"
 
 namespace lbmd {
 
@@ -48,6 +49,11 @@ cudaError_t launch_lb_stream_collide_fluct(int storage, const LbGeom &g, const L
     case LBMD_STORE_BF16: return fluct_launch<LBMD_STORE_BF16>(g, ph, src, dst, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_lb_aa_fluct(int storage, const LbGeom &g, const LbPhys &ph, void *buf,
+                               int odd, cudaStream_t s) {
+  return aa_launch_storage<true>(storage, g, ph, buf, odd, nullptr, s);
 }
 
 void fluct_amplitudes(double kT, double tau, float amp[15]) {

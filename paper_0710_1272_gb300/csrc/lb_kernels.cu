@@ -90,15 +90,17 @@ cudaError_t launch_link_mask(const LbGeom &g, uint32_t *mask, cudaStream_t s) {
 //   h*_q(y) = f_eq,opp(q)(y) - w_q rho0      otherwise (bounce-back source),
 // at fluid nodes y, and zero at solid nodes.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void init_fields_at(int x, int y, int z, const LbGeom &g, float rho0,
-                                               const float *rho, const float *u, float tg_amp,
-                                               float &r, float &ux, float &uy, float &uz) {
-  const size_t c = ((size_t)z * g.ny + y) * g.nx + x;
+// Initial (rho, u) of node (x, y): entry c of the given fields (component
+// stride ustride), else rho0 and the Taylor-Green flow of amplitude tg_amp.
+__device__ __forceinline__ void fields_at(int x, int y, size_t c, long long ustride,
+                                          const LbGeom &g, float rho0, const float *rho,
+                                          const float *u, float tg_amp, float &r, float &ux,
+                                          float &uy, float &uz) {
   r = rho ? rho[c] : rho0;
   if (u) {
     ux = u[c];
-    uy = u[(size_t)g.V + c];
-    uz = u[2 * (size_t)g.V + c];
+    uy = u[(size_t)ustride + c];
+    uz = u[2 * (size_t)ustride + c];
   } else if (tg_amp != 0.f) {
     float sx, cxv, sy, cyv;
     sincospif(2.0f * (float)x / (float)g.nx, &sx, &cxv);
@@ -111,10 +113,19 @@ __device__ __forceinline__ void init_fields_at(int x, int y, int z, const LbGeom
   }
 }
 
+__device__ __forceinline__ void init_fields_at(int x, int y, int z, const LbGeom &g, float rho0,
+                                               const float *rho, const float *u, float tg_amp,
+                                               float &r, float &ux, float &uy, float &uz) {
+  fields_at(x, y, ((size_t)z * g.ny + y) * g.nx + x, g.V, g, rho0, rho, u, tg_amp, r, ux, uy, uz);
+}
+
+// f_eq,p - w_p rho0 (Eq. 6), every operation rounded explicitly so that the
+// pull and in-place initialisations produce the same bits.
 __device__ __forceinline__ float feq_dev(int p, float r, float rho0, float ux, float uy, float uz) {
-  const float cu = cx(p) * ux + cy(p) * uy + cz(p) * uz;
-  const float usq = ux * ux + uy * uy + uz * uz;
-  return wq(p) * ((r - rho0) + r * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
+  const float cu = cx(p) * ux + cy(p) * uy + cz(p) * uz;  // +-u_a sums
+  const float usq = fmaf(uz, uz, fmaf(uy, uy, __fmul_rn(ux, ux)));
+  const float poly = fmaf(-1.5f, usq, fmaf(__fmul_rn(4.5f, cu), cu, __fmul_rn(3.0f, cu)));
+  return __fmul_rn(wq(p), fmaf(r, poly, r - rho0));
 }
 
 template <int S>
@@ -171,13 +182,58 @@ cudaError_t launch_init_populations(int storage, const LbGeom &g, float rho0, co
   return cudaGetLastError();
 }
 
+// In-place streaming starts from the pre-collision state itself, stored
+// locally (kPopAALocal): h_q(x, 0) = f_eq,q(rho(x), u(x)) - w_q rho0 at fluid
+// nodes, zero at solid nodes.  One z-slab per launch; rho / u are the slab's.
+template <int S>
+__global__ void k_init_local(LbGeom g, float rho0, const float *rho, const float *u,
+                             long long ustride, float tg_amp, int z0,
+                             typename Store<S>::T *__restrict__ dst) {
+  using St = Store<S>;
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * kRowsPerBlock + threadIdx.y;
+  const int z = z0 + blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
+  const size_t Vp = (size_t)g.Vp;
+  float r = rho0, ux = 0.f, uy = 0.f, uz = 0.f;
+  const bool solid = solid_at(g.solid, g.ntx, g.ny, x, y, z);
+  if (!solid)
+    fields_at(x, y, ((size_t)blockIdx.z * g.ny + y) * g.nx + x, ustride, g, rho0, rho, u, tg_amp, r,
+              ux, uy, uz);
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) St::store(dst + q * Vp + self, solid ? 0.f : feq_dev(q, r, rho0, ux, uy, uz));
+}
+
+cudaError_t launch_init_local(int storage, const LbGeom &g, float rho0, const float *rho,
+                              const float *u, long long ustride, float tg_amp, long long z0,
+                              long long nzc, void *dst, cudaStream_t s) {
+  dim3 block(32, kRowsPerBlock);
+  dim3 grid(g.ntx, (g.ny + kRowsPerBlock - 1) / kRowsPerBlock, (unsigned)nzc);
+  switch (storage) {
+    case LBMD_STORE_F32:
+      k_init_local<LBMD_STORE_F32><<<grid, block, 0, s>>>(g, rho0, rho, u, ustride, tg_amp, (int)z0, (float *)dst);
+      break;
+    case LBMD_STORE_F16:
+      k_init_local<LBMD_STORE_F16><<<grid, block, 0, s>>>(g, rho0, rho, u, ustride, tg_amp, (int)z0, (__half *)dst);
+      break;
+    case LBMD_STORE_BF16:
+      k_init_local<LBMD_STORE_BF16><<<grid, block, 0, s>>>(g, rho0, rho, u, ustride, tg_amp, (int)z0, (__nv_bfloat16 *)dst);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
-// Read-outs over the z-slab [z0, z0 + nzc): moments (Eqs. 7-8) and the pulled
-// pre-collision populations.  Solid nodes read zero.
+// Read-outs over the z-slab [z0, z0 + nzc): moments (Eqs. 7-8) and the
+// pre-collision populations, fetched for the layout `mode` (kPop*).  Solid
+// nodes read zero.
 // ---------------------------------------------------------------------------
 template <int S>
 __global__ void k_read_moments(LbGeom g, LbPhys ph, const typename Store<S>::T *__restrict__ src,
-                               int z0, float *rho, float *u, long long ustride) {
+                               int mode, int z0, float *rho, float *u, long long ustride) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * kRowsPerBlock + threadIdx.y;
   const int z = z0 + blockIdx.z;
@@ -189,7 +245,7 @@ __global__ void k_read_moments(LbGeom g, LbPhys ph, const typename Store<S>::T *
     return;
   }
   float h[kQ];
-  pull19<S, true>(g, src, x, y, z, h);
+  fetch19<S>(g, src, x, y, z, mode, h);
   float drho, jx, jy, jz;
   moments19(h, drho, jx, jy, jz);
   const float r = ph.rho0 + drho;
@@ -208,7 +264,7 @@ __global__ void k_read_moments(LbGeom g, LbPhys ph, const typename Store<S>::T *
 
 template <int S>
 __global__ void k_read_pulled(LbGeom g, float rho0, const typename Store<S>::T *__restrict__ src,
-                              int z0, float *f, long long fstride) {
+                              int mode, int z0, float *f, long long fstride) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * kRowsPerBlock + threadIdx.y;
   const int z = z0 + blockIdx.z;
@@ -220,25 +276,25 @@ __global__ void k_read_pulled(LbGeom g, float rho0, const typename Store<S>::T *
     return;
   }
   float h[kQ];
-  pull19<S, true>(g, src, x, y, z, h);
+  fetch19<S>(g, src, x, y, z, mode, h);
 #pragma unroll
-  for (int p = 0; p < kQ; ++p) f[p * fstride + o] = wq(p) * rho0 + h[p];
+  for (int p = 0; p < kQ; ++p) f[p * fstride + o] = __fadd_rn(__fmul_rn(wq(p), rho0), h[p]);
 }
 
 cudaError_t launch_read_moments(int storage, const LbGeom &g, const LbPhys &ph, const void *src,
-                                long long z0, long long nzc, float *rho, float *u,
+                                int mode, long long z0, long long nzc, float *rho, float *u,
                                 long long ustride, cudaStream_t s) {
   dim3 block(32, kRowsPerBlock);
   dim3 grid(g.ntx, (g.ny + kRowsPerBlock - 1) / kRowsPerBlock, (unsigned)nzc);
   switch (storage) {
     case LBMD_STORE_F32:
-      k_read_moments<LBMD_STORE_F32><<<grid, block, 0, s>>>(g, ph, (const float *)src, (int)z0, rho, u, ustride);
+      k_read_moments<LBMD_STORE_F32><<<grid, block, 0, s>>>(g, ph, (const float *)src, mode, (int)z0, rho, u, ustride);
       break;
     case LBMD_STORE_F16:
-      k_read_moments<LBMD_STORE_F16><<<grid, block, 0, s>>>(g, ph, (const __half *)src, (int)z0, rho, u, ustride);
+      k_read_moments<LBMD_STORE_F16><<<grid, block, 0, s>>>(g, ph, (const __half *)src, mode, (int)z0, rho, u, ustride);
       break;
     case LBMD_STORE_BF16:
-      k_read_moments<LBMD_STORE_BF16><<<grid, block, 0, s>>>(g, ph, (const __nv_bfloat16 *)src, (int)z0, rho, u, ustride);
+      k_read_moments<LBMD_STORE_BF16><<<grid, block, 0, s>>>(g, ph, (const __nv_bfloat16 *)src, mode, (int)z0, rho, u, ustride);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -247,19 +303,19 @@ cudaError_t launch_read_moments(int storage, const LbGeom &g, const LbPhys &ph, 
 }
 
 cudaError_t launch_read_pulled(int storage, const LbGeom &g, float rho0, const void *src,
-                               long long z0, long long nzc, float *f, long long fstride,
-                               cudaStream_t s) {
+                               int mode, long long z0, long long nzc, float *f,
+                               long long fstride, cudaStream_t s) {
   dim3 block(32, kRowsPerBlock);
   dim3 grid(g.ntx, (g.ny + kRowsPerBlock - 1) / kRowsPerBlock, (unsigned)nzc);
   switch (storage) {
     case LBMD_STORE_F32:
-      k_read_pulled<LBMD_STORE_F32><<<grid, block, 0, s>>>(g, rho0, (const float *)src, (int)z0, f, fstride);
+      k_read_pulled<LBMD_STORE_F32><<<grid, block, 0, s>>>(g, rho0, (const float *)src, mode, (int)z0, f, fstride);
       break;
     case LBMD_STORE_F16:
-      k_read_pulled<LBMD_STORE_F16><<<grid, block, 0, s>>>(g, rho0, (const __half *)src, (int)z0, f, fstride);
+      k_read_pulled<LBMD_STORE_F16><<<grid, block, 0, s>>>(g, rho0, (const __half *)src, mode, (int)z0, f, fstride);
       break;
     case LBMD_STORE_BF16:
-      k_read_pulled<LBMD_STORE_BF16><<<grid, block, 0, s>>>(g, rho0, (const __nv_bfloat16 *)src, (int)z0, f, fstride);
+      k_read_pulled<LBMD_STORE_BF16><<<grid, block, 0, s>>>(g, rho0, (const __nv_bfloat16 *)src, mode, (int)z0, f, fstride);
       break;
     default:
       return cudaErrorInvalidValue;

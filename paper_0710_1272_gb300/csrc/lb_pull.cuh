@@ -1,5 +1,5 @@
 // lb_pull.cuh -- pull streaming with halfway bounce-back, shared by the
-// stream-collide kernel, the read-out kernels and the bead gather.
+// stream-collide kernels, the read-out kernels and the bead gather.
 #pragma once
 
 #include "lbmd_common.cuh"
@@ -12,10 +12,11 @@ namespace lbmd {
 //   h_p(x) = h*_opp(p)(x)       otherwise (the population that left x towards
 //                               the solid node comes back reversed),
 // where bit p of `bb` says whether x - c_p is solid (the node's link mask; 0
-// for a node known to be far from any solid node).  I is the index type of
-// the population offsets: int when 19 Vp < 2^31 (cheaper address
-// arithmetic), size_t otherwise.
-template <int S, typename I = size_t>
+// for a node known to be far from any solid node).  h*_q(y) sits at [q][y]
+// (SWAP = false, kPopPull) or at [opp(q)][y] (SWAP = true, kPopAASwap).  I is
+// the index type of the population offsets: int when 19 Vp < 2^31 (cheaper
+// address arithmetic), size_t otherwise.
+template <int S, typename I = size_t, bool SWAP = false>
 __device__ __forceinline__ void pull19_mask(const LbGeom &g,
                                             const typename Store<S>::T *__restrict__ src, int x,
                                             int y, int z, uint32_t bb, float h[kQ]) {
@@ -32,19 +33,35 @@ __device__ __forceinline__ void pull19_mask(const LbGeom &g,
     const int sx = cx(p) == 1 ? xm : (cx(p) == -1 ? xp : x);
     const int sy = cy(p) == 1 ? ym : (cy(p) == -1 ? yp : y);
     const int sz = cz(p) == 1 ? zm : (cz(p) == -1 ? zp : z);
-    const I sidx = (I)p * Vp + ((I)sz * ny + sy) * nx + sx;
-    const I bidx = (I)opp(p) * Vp + self;
+    const I sidx = (I)(SWAP ? opp(p) : p) * Vp + ((I)sz * ny + sy) * nx + sx;
+    const I bidx = (I)(SWAP ? p : opp(p)) * Vp + self;
     h[p] = St::load(src + (((bb >> p) & 1u) ? bidx : sidx));
   }
 }
 
-// As pull19_mask; CHECK = false skips the link mask (tile known to be far
-// from any solid node).
-template <int S, bool CHECK, typename I = size_t>
-__device__ __forceinline__ void pull19(const LbGeom &g, const typename Store<S>::T *__restrict__ src,
-                                       int x, int y, int z, float h[kQ]) {
-  const uint32_t bb = CHECK ? __ldg(&g.lmask[((I)z * g.ny + y) * g.nx + x]) : 0u;
-  pull19_mask<S, I>(g, src, x, y, z, bb, h);
+__device__ __forceinline__ bool tile_is_near(const LbGeom &g, int x, int y, int z) {
+  return __ldg(&g.tile_near[((size_t)z * g.ny + y) * g.ntx + (x >> 5)]) != 0;
+}
+
+// Pre-collision deviations h_p(x, t) of fluid node (x, y, z) for populations
+// held in layout `mode` (kPop*), taking the link mask only where a solid node
+// is within one node of the node's tile.  For read-outs and the bead gather,
+// which run while no kernel writes `src`.
+template <int S, typename I = size_t>
+__device__ __forceinline__ void fetch19(const LbGeom &g, const typename Store<S>::T *__restrict__ src,
+                                        int x, int y, int z, int mode, float h[kQ]) {
+  using St = Store<S>;
+  const I self = ((I)z * g.ny + y) * g.nx + x;
+  if (mode == kPopAALocal) {
+#pragma unroll
+    for (int p = 0; p < kQ; ++p) h[p] = St::load(src + (I)p * (I)g.Vp + self);
+    return;
+  }
+  const uint32_t bb = tile_is_near(g, x, y, z) ? __ldg(&g.lmask[self]) : 0u;
+  if (mode == kPopAASwap)
+    pull19_mask<S, I, true>(g, src, x, y, z, bb, h);
+  else
+    pull19_mask<S, I, false>(g, src, x, y, z, bb, h);
 }
 
 // rho - rho0 and the momentum sum_p h_p c_p (sum_p w_p c_p = 0).
@@ -59,10 +76,6 @@ __device__ __forceinline__ void moments19(const float h[kQ], float &drho, float 
     if (cy(p)) jy += cy(p) > 0 ? h[p] : -h[p];
     if (cz(p)) jz += cz(p) > 0 ? h[p] : -h[p];
   }
-}
-
-__device__ __forceinline__ bool tile_is_near(const LbGeom &g, int x, int y, int z) {
-  return __ldg(&g.tile_near[((size_t)z * g.ny + y) * g.ntx + (x >> 5)]) != 0;
 }
 
 }  // namespace lbmd

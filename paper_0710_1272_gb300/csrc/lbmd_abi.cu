@@ -25,8 +25,10 @@ struct lbmd_ctx {
   LbPhys phys;
   ChainArgs chain;
   char *ws;
-  char *pop[2];
-  int cur;  // pop[cur] holds the post-collision populations of the last step
+  char *pop[2];  // equal with in-place streaming
+  int cur;  // pull: pop[cur] holds the post-collision populations of the last
+            // step; in place: 0 = kPopAALocal, 1 = kPopAASwap
+  int aa;   // in-place (AA-pattern) streaming
   int N, has_bonds;
   cudaStream_t user;        // caller's stream
   cudaStream_t own, side;   // private streams: steps run on own, MD on side
@@ -63,14 +65,21 @@ int cuda_fail(lbmd_ctx *c, cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
-// Enqueue one coupled LB step reading pop[src] and writing pop[1 - src] on
-// the private stream `own`: the MD cycle (gather + M substeps) on the side
-// stream concurrently with the stream-collide, then the spread of the bead
-// impulses into the new post-collision populations.  With paper forcing the
-// bead source does not depend on f, so adding it after the collision is exact.
+// Layout (kPop*) of the populations when the context's `cur` is `src`.
+int pop_mode(const lbmd_ctx *c, int src) {
+  return c->aa ? (src ? kPopAASwap : kPopAALocal) : kPopPull;
+}
+
+// Enqueue one coupled LB step reading pop[src] and writing pop[1 - src] (with
+// in-place streaming: the one buffer, even step if src = 0, odd if 1) on the
+// private stream `own`: the MD cycle (gather + M substeps) on the side stream
+// concurrently with the stream-collide, then the spread of the bead impulses
+// into the new post-collision populations.  With paper forcing the bead source
+// does not depend on f, so adding it after the collision is exact.
 cudaError_t enqueue_step(lbmd_ctx *c, int src) {
   const void *A = c->pop[src];
   void *B = c->pop[1 - src];
+  const int mode_out = pop_mode(c, 1 - src);
   cudaError_t e;
   cudaEvent_t t[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   if (c->timing) {
@@ -93,7 +102,7 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     for (int k : {0, 1, 4})
       if (t[k] && (e = cudaEventRecord(t[k], c->own)) != cudaSuccess) return e;
     if ((e = launch_spread(c->p.storage, c->geo, c->chain.sp_node, c->chain.sp_w, c->chain.J, c->N,
-                           8 * c->N, B, c->status, c->own)) != cudaSuccess)
+                           8 * c->N, B, mode_out, c->status, c->own)) != cudaSuccess)
       return e;
     if (t[5] && (e = cudaEventRecord(t[5], c->own)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -103,6 +112,7 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     // on the side stream while the stream-collide runs on the main one
     ChainArgs a = c->chain;
     a.f = A;
+    a.f_mode = pop_mode(c, src);
     if (t[2] && (e = cudaEventRecord(t[2], c->own)) != cudaSuccess) return e;
     if ((e = launch_gather(c->p.storage, a, c->own)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(c->ev_fork, c->own)) != cudaSuccess) return e;
@@ -114,15 +124,18 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     if ((e = cudaEventRecord(t[3], c->own)) != cudaSuccess) return e;
   }
   if (t[0] && (e = cudaEventRecord(t[0], c->own)) != cudaSuccess) return e;
+  DevStatus *bump = c->N > 0 ? nullptr : c->status;
   if (c->phys.step) {
     // thermal source: the kernel reads the step count, so a box without
     // beads advances it in a separate launch afterwards
-    if ((e = launch_lb_stream_collide_fluct(c->p.storage, c->geo, c->phys, A, B, c->own)) != cudaSuccess)
-      return e;
+    e = c->aa ? launch_lb_aa_fluct(c->p.storage, c->geo, c->phys, B, src, c->own)
+              : launch_lb_stream_collide_fluct(c->p.storage, c->geo, c->phys, A, B, c->own);
+    if (e != cudaSuccess) return e;
     if (c->N == 0 && (e = launch_bump_step(c->status, c->own)) != cudaSuccess) return e;
-  } else if ((e = launch_lb_stream_collide(c->p.storage, c->geo, c->phys, A, B,
-                                           c->N > 0 ? nullptr : c->status, c->own)) != cudaSuccess) {
-    return e;
+  } else {
+    e = c->aa ? launch_lb_aa(c->p.storage, c->geo, c->phys, B, src, bump, c->own)
+              : launch_lb_stream_collide(c->p.storage, c->geo, c->phys, A, B, bump, c->own);
+    if (e != cudaSuccess) return e;
   }
   if (t[1] && (e = cudaEventRecord(t[1], c->own)) != cudaSuccess) return e;
   if (c->N > 0) {
@@ -130,7 +143,7 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     if ((e = cudaStreamWaitEvent(c->own, c->ev_join, 0)) != cudaSuccess) return e;
     if (t[4] && (e = cudaEventRecord(t[4], c->own)) != cudaSuccess) return e;
     if ((e = launch_spread(c->p.storage, c->geo, c->chain.sp_node, c->chain.sp_w, c->chain.J, c->N,
-                           8 * c->N, B, c->status, c->own)) != cudaSuccess)
+                           8 * c->N, B, mode_out, c->status, c->own)) != cudaSuccess)
       return e;
     if (t[5] && (e = cudaEventRecord(t[5], c->own)) != cudaSuccess) return e;
   } else if (t[4]) {
@@ -239,6 +252,7 @@ int lbmd_create(const lbmd_params *params, void *dev_workspace, size_t bytes, vo
   c->pop[0] = c->ws + L.popA;
   c->pop[1] = c->ws + L.popB;
   c->cur = 0;
+  c->aa = p.streaming == LBMD_STREAM_AA ? 1 : 0;
   c->user = (cudaStream_t)cuda_stream;
   c->N = p.n_beads;
   c->has_bonds = params_have_bonds(p) ? 1 : 0;
@@ -310,8 +324,9 @@ int lbmd_read_fields(lbmd_ctx *c, float *rho, float *u, int dst_is_device) {
   if (!rho && !u) return LBMD_OK;
   const LbGeom &g = c->geo;
   const void *src = c->pop[c->cur];
+  const int mode = pop_mode(c, c->cur);
   if (dst_is_device) {
-    CK(c, launch_read_moments(c->p.storage, g, c->phys, src, 0, g.nz, rho, u, g.V, c->user));
+    CK(c, launch_read_moments(c->p.storage, g, c->phys, src, mode, 0, g.nz, rho, u, g.V, c->user));
     return LBMD_OK;
   }
   const long long plane = (long long)g.nx * g.ny;
@@ -320,7 +335,7 @@ int lbmd_read_fields(lbmd_ctx *c, float *rho, float *u, int dst_is_device) {
   for (long long z0 = 0; z0 < g.nz; z0 += nzc_max) {
     const long long nzc = std::min(nzc_max, (long long)g.nz - z0);
     const long long cells = nzc * plane;
-    CK(c, launch_read_moments(c->p.storage, g, c->phys, src, z0, nzc, rho ? srho : nullptr,
+    CK(c, launch_read_moments(c->p.storage, g, c->phys, src, mode, z0, nzc, rho ? srho : nullptr,
                               u ? su : nullptr, cells, c->user));
     if (rho)
       CK(c, cudaMemcpyAsync(rho + z0 * plane, srho, cells * 4, cudaMemcpyDeviceToHost, c->user));
@@ -339,8 +354,9 @@ int lbmd_read_populations(lbmd_ctx *c, float *f, int dst_is_device) {
   if (!f) return fail(LBMD_EINVAL, "f is NULL");
   const LbGeom &g = c->geo;
   const void *src = c->pop[c->cur];
+  const int mode = pop_mode(c, c->cur);
   if (dst_is_device) {
-    CK(c, launch_read_pulled(c->p.storage, g, (float)c->p.rho0, src, 0, g.nz, f, g.V, c->user));
+    CK(c, launch_read_pulled(c->p.storage, g, (float)c->p.rho0, src, mode, 0, g.nz, f, g.V, c->user));
     return LBMD_OK;
   }
   const long long plane = (long long)g.nx * g.ny;
@@ -348,7 +364,8 @@ int lbmd_read_populations(lbmd_ctx *c, float *f, int dst_is_device) {
   for (long long z0 = 0; z0 < g.nz; z0 += nzc_max) {
     const long long nzc = std::min(nzc_max, (long long)g.nz - z0);
     const long long cells = nzc * plane;
-    CK(c, launch_read_pulled(c->p.storage, g, (float)c->p.rho0, src, z0, nzc, c->stage, cells, c->user));
+    CK(c, launch_read_pulled(c->p.storage, g, (float)c->p.rho0, src, mode, z0, nzc, c->stage, cells,
+                             c->user));
     for (int q = 0; q < 19; ++q)
       CK(c, cudaMemcpyAsync(f + q * g.V + z0 * plane, c->stage + q * cells, cells * 4,
                             cudaMemcpyDeviceToHost, c->user));

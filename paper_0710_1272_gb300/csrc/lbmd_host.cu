@@ -58,7 +58,8 @@ Layout make_layout(const lbmd_params &p, bool with_stage) {
     return at;
   };
   L.popA = take((size_t)19 * L.Vp * store_bytes(p.storage));
-  L.popB = take((size_t)19 * L.Vp * store_bytes(p.storage));
+  // in-place streaming keeps a single population buffer
+  L.popB = p.streaming == LBMD_STREAM_AA ? L.popA : take((size_t)19 * L.Vp * store_bytes(p.storage));
   L.solid = take(rows * L.ntx * sizeof(uint32_t));
   L.tile = take(rows * L.ntx);
   L.lmask = take((size_t)V * sizeof(uint32_t));
@@ -114,6 +115,8 @@ int validate(const lbmd_params *p) {
   if (p->solvent_free != 0 && p->solvent_free != 1)
     return fail(LBMD_EINVAL, "solvent_free must be 0 or 1");
   if (p->solvent_free && p->n_beads < 1) return fail(LBMD_EINVAL, "solvent_free needs n_beads >= 1");
+  if (p->streaming != LBMD_STREAM_PULL && p->streaming != LBMD_STREAM_AA)
+    return fail(LBMD_EINVAL, "unknown streaming %d", p->streaming);
   if (!(p->kT_fluid >= 0) || !std::isfinite(p->kT_fluid))
     return fail(LBMD_EINVAL, "kT_fluid must be >= 0");
   if (p->diag_every < 0 || p->diag_capacity < 0)
@@ -297,24 +300,56 @@ cudaError_t init_instance(const lbmd_params &p, const Layout &L, char *ws, cudaS
     out.phys.step = &out.status->step;
   }
 
-  // initial populations: (rho, u) staged in the second population buffer
-  const float *drho = nullptr, *du = nullptr;
+  // initial populations
   std::vector<float> hfield;
   if (p.init_rho || p.init_u) {
     const size_t V = (size_t)g.V;
     hfield.assign(4 * V, 0.f);
     for (size_t k = 0; k < V; ++k) hfield[k] = p.init_rho ? (float)p.init_rho[k] : (float)p.rho0;
     for (size_t k = 0; k < 3 * V; ++k) hfield[V + k] = p.init_u ? (float)p.init_u[k] : 0.f;
-    UP(cudaMemcpyAsync(out.pop[1], hfield.data(), hfield.size() * 4, cudaMemcpyHostToDevice, s), "upload");
-    drho = p.init_rho ? (const float *)out.pop[1] : nullptr;
-    du = p.init_u ? (const float *)out.pop[1] + V : nullptr;
   }
-  UP(launch_init_populations(p.storage, g, (float)p.rho0, drho, du, (float)p.init_tg_amp, out.pop[0], s),
-     "init kernel");
-  // the second buffer must hold zeros at solid nodes too: copy the first
-  UP(cudaMemcpyAsync(out.pop[1], out.pop[0], (size_t)19 * L.Vp * store_bytes(p.storage),
-                     cudaMemcpyDeviceToDevice, s),
-     "copy");
+  if (p.streaming == LBMD_STREAM_AA) {
+    // one buffer, f_eq stored locally; given fields go through the staging
+    // buffer (19 floats per cell of a chunk) one z-slab at a time
+    if (hfield.empty()) {
+      UP(launch_init_local(p.storage, g, (float)p.rho0, nullptr, nullptr, 0, (float)p.init_tg_amp, 0,
+                           g.nz, out.pop[0], s),
+         "init kernel");
+    } else {
+      if (L.stage_floats == 0) {
+        *what = "in-place streaming with initial fields needs the staging buffer";
+        return cudaErrorInvalidValue;
+      }
+      const long long plane = (long long)g.nx * g.ny;
+      const long long nzc_max = std::max(1LL, L.chunk_cells / plane);
+      float *st = (float *)(ws + L.stage);
+      for (long long z0 = 0; z0 < g.nz; z0 += nzc_max) {
+        const long long nzc = std::min(nzc_max, (long long)g.nz - z0), cells = nzc * plane;
+        for (int a = 0; a < 4; ++a)
+          UP(cudaMemcpyAsync(st + a * cells, hfield.data() + a * (size_t)g.V + z0 * plane, cells * 4,
+                             cudaMemcpyHostToDevice, s),
+             "upload");
+        UP(launch_init_local(p.storage, g, (float)p.rho0, p.init_rho ? st : nullptr,
+                             p.init_u ? st + cells : nullptr, cells, (float)p.init_tg_amp, z0, nzc,
+                             out.pop[0], s),
+           "init kernel");
+      }
+    }
+  } else {
+    // (rho, u) staged in the second population buffer
+    const float *drho = nullptr, *du = nullptr;
+    if (!hfield.empty()) {
+      UP(cudaMemcpyAsync(out.pop[1], hfield.data(), hfield.size() * 4, cudaMemcpyHostToDevice, s), "upload");
+      drho = p.init_rho ? (const float *)out.pop[1] : nullptr;
+      du = p.init_u ? (const float *)out.pop[1] + g.V : nullptr;
+    }
+    UP(launch_init_populations(p.storage, g, (float)p.rho0, drho, du, (float)p.init_tg_amp, out.pop[0], s),
+       "init kernel");
+    // the second buffer must hold zeros at solid nodes too: copy the first
+    UP(cudaMemcpyAsync(out.pop[1], out.pop[0], (size_t)19 * L.Vp * store_bytes(p.storage),
+                       cudaMemcpyDeviceToDevice, s),
+       "copy");
+  }
 
   // beads, in a local frame at the integer origin floor(r_0)
   DevStatus st{};

@@ -56,8 +56,9 @@ struct Instance {
   int has_bonds;
 };
 
-// Uploads the geometry, the initial populations (post-collision buffer pop[0]
-// such that the first pull gives f_eq(rho, u)), the beads and the status
+// Uploads the geometry, the initial populations (pull streaming: post-collision
+// buffer pop[0] such that the first pull gives f_eq(rho, u); in-place
+// streaming: f_eq(rho, u) itself, kPopAALocal), the beads and the status
 // word of box `p` into the workspace slice `ws` laid out by `L`, on stream s,
 // and synchronises s (the host staging must outlive the copies).  On error
 // returns the CUDA error and sets *what.

@@ -52,6 +52,19 @@ struct LbGeom {
                                 // pull source x - c_p is solid, bit 0 if x is
 };
 
+// Where the populations of a box are held between two steps; this decides
+// how the pre-collision value h_p(x, t) is fetched and where the bead source
+// of stage (3) is added.
+//   kPopPull:    two-buffer pull streaming; the buffer holds the post-collision
+//                h*_p(x) of the last step at [p][x].
+//   kPopAALocal: in-place (AA) streaming after an odd step (and at the start):
+//                the buffer holds the pre-collision h_p(x, t) at [p][x].
+//   kPopAASwap:  in-place streaming after an even step: the buffer holds the
+//                post-collision h*_p(x) at [opp(p)][x].
+constexpr int kPopPull = 0;
+constexpr int kPopAALocal = 1;
+constexpr int kPopAASwap = 2;
+
 // Collision variant for a zero body force: both forcing schemes then reduce
 // to plain BGK (no velocity shift, no source term), so the kernels skip them.
 constexpr int kForcingNone = 2;
@@ -70,8 +83,8 @@ struct LbPhys {
 // Everything the MD kernel needs for one chain.
 struct ChainArgs {
   LbGeom geo;
-  const void *f;            // populations to gather from (post-collision of the
-                            // previous step; pulled on the fly)
+  const void *f;            // populations to gather from (kPop* layout f_mode)
+  int f_mode;
   const uint8_t *xslab;     // [nx]: 1 if the x-layer holds a solid node
   int has_wall, wall_x, wall_t, pore_d, pore_y0, pore_z0;
   float rho0, g[3];
@@ -149,16 +162,31 @@ cudaError_t launch_link_mask(const LbGeom &g, uint32_t *mask, cudaStream_t s);
 cudaError_t launch_init_populations(int storage, const LbGeom &g, float rho0,
                                     const float *rho, const float *u, float tg_amp,
                                     void *dst, cudaStream_t s);
+// In-place streaming: f = f_eq(rho, u) stored locally (kPopAALocal) on the
+// z-slab [z0, z0 + nzc); rho / u (or null) hold the slab's fields with
+// component stride `ustride`.
+cudaError_t launch_init_local(int storage, const LbGeom &g, float rho0, const float *rho,
+                              const float *u, long long ustride, float tg_amp, long long z0,
+                              long long nzc, void *dst, cudaStream_t s);
+// One in-place (AA-pattern) stream-collide on `buf`: odd = 0 takes the buffer
+// from kPopAALocal to kPopAASwap, odd = 1 back.  `bump` as for
+// launch_lb_stream_collide; the _fluct variant adds the thermal source.
+cudaError_t launch_lb_aa(int storage, const LbGeom &g, const LbPhys &ph, void *buf, int odd,
+                         DevStatus *bump, cudaStream_t s);
+cudaError_t launch_lb_aa_fluct(int storage, const LbGeom &g, const LbPhys &ph, void *buf,
+                               int odd, cudaStream_t s);
+// Read-outs of the pre-collision state of populations held in layout `mode`.
 cudaError_t launch_read_moments(int storage, const LbGeom &g, const LbPhys &ph,
-                                const void *src, long long z0, long long nzc,
+                                const void *src, int mode, long long z0, long long nzc,
                                 float *rho, float *u, long long ustride, cudaStream_t s);
 cudaError_t launch_read_pulled(int storage, const LbGeom &g, float rho0, const void *src,
-                               long long z0, long long nzc, float *f, long long fstride,
-                               cudaStream_t s);
+                               int mode, long long z0, long long nzc, float *f,
+                               long long fstride, cudaStream_t s);
 cudaError_t launch_gather(int storage, const ChainArgs &a, cudaStream_t s);
 cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s);
+// Spread into the post-collision populations of `dst`, held in layout `mode`.
 cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, const float *sp_w,
-                          const float4 *J, int N, int nw, void *dst, DevStatus *bump,
+                          const float4 *J, int N, int nw, void *dst, int mode, DevStatus *bump,
                           cudaStream_t s);
 // Ensemble launchers.  `live` points at the flags of the current step (one int
 // per realisation); realisations whose flag is 0 are skipped by every kernel.

@@ -769,10 +769,7 @@ __device__ F3 gather_pair(const ChainArgs &a, const void *f, int e, bool valid) 
       const int x = node % g.nx, yz = node / g.nx;
       const int y = yz % g.ny, z = yz / g.ny;
       float h[kQ];
-      if (tile_is_near(g, x, y, z))
-        pull19<S, true>(g, (const T *)f, x, y, z, h);
-      else
-        pull19<S, false>(g, (const T *)f, x, y, z, h);
+      fetch19<S>(g, (const T *)f, x, y, z, a.f_mode, h);
       float drho, jx, jy, jz;
       moments19(h, drho, jx, jy, jz);
       if (a.forcing == LBMD_FORCING_GUO) {
@@ -863,12 +860,15 @@ cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // (3) extrapolation of the forces: node x_k receives -w_ik J_i as the source
 // S_p = 3 w_p c_p . F (Eq. 10, reaction sign) added to the post-collision
-// populations.  Lanes of a warp that hit the same node sum their vectors
-// first (in lane order), and one lane issues the 18 atomic adds.
+// populations h*_p(x_k), wherever layout `mode` holds them: [p][x_k] (pull),
+// [opp(p)][x_k] (in place, after an even step), or [p][x_k + c_p] --
+// [opp(p)][x_k] if x_k + c_p is solid -- (in place, after an odd step).
+// Lanes of a warp that hit the same node sum their vectors first (in lane
+// order), and one lane issues the 18 atomic adds.
 // ---------------------------------------------------------------------------
 template <int S>
 __global__ void k_spread(LbGeom g, const int *__restrict__ sp_node, const float *__restrict__ sp_w,
-                         const float4 *__restrict__ J, int nw, typename Store<S>::T *dst,
+                         const float4 *__restrict__ J, int nw, typename Store<S>::T *dst, int mode,
                          DevStatus *bump) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (bump != nullptr && e == 0) bump->step += 1;
@@ -897,29 +897,44 @@ __global__ void k_spread(LbGeom g, const int *__restrict__ sp_node, const float 
   if (node >= 0 && lane == leader) {
     using St = Store<S>;
     const size_t Vp = (size_t)g.Vp;
+    if (mode == kPopAALocal) {
+      const int x = node % g.nx, yz = node / g.nx;
+      const int y = yz % g.ny, z = yz / g.ny;
+      const uint32_t bb = __ldg(&g.lmask[node]);  // bit opp(p): x_k + c_p is solid
 #pragma unroll
-    for (int p = 1; p < kQ; ++p) {
-      const float cf = cx(p) * sum.x + cy(p) * sum.y + cz(p) * sum.z;
-      St::add(dst + (size_t)p * Vp + node, 3.0f * wq(p) * cf);
+      for (int p = 1; p < kQ; ++p) {
+        const float cf = cx(p) * sum.x + cy(p) * sum.y + cz(p) * sum.z;
+        const size_t t = ((size_t)wrapi(z + cz(p), g.nz) * g.ny + wrapi(y + cy(p), g.ny)) * g.nx +
+                         wrapi(x + cx(p), g.nx);
+        const size_t slot = ((bb >> opp(p)) & 1u) ? (size_t)opp(p) * Vp + node : (size_t)p * Vp + t;
+        St::add(dst + slot, 3.0f * wq(p) * cf);
+      }
+    } else {
+#pragma unroll
+      for (int p = 1; p < kQ; ++p) {
+        const float cf = cx(p) * sum.x + cy(p) * sum.y + cz(p) * sum.z;
+        const int q = mode == kPopAASwap ? opp(p) : p;
+        St::add(dst + (size_t)q * Vp + node, 3.0f * wq(p) * cf);
+      }
     }
   }
 }
 
 cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, const float *sp_w,
-                          const float4 *J, int N, int nw, void *dst, DevStatus *bump,
+                          const float4 *J, int N, int nw, void *dst, int mode, DevStatus *bump,
                           cudaStream_t s) {
   (void)N;
   const int threads = 256;
   const int blocks = nw > 0 ? (nw + threads - 1) / threads : 1;
   switch (storage) {
     case LBMD_STORE_F32:
-      k_spread<LBMD_STORE_F32><<<blocks, threads, 0, s>>>(g, sp_node, sp_w, J, nw, (float *)dst, bump);
+      k_spread<LBMD_STORE_F32><<<blocks, threads, 0, s>>>(g, sp_node, sp_w, J, nw, (float *)dst, mode, bump);
       break;
     case LBMD_STORE_F16:
-      k_spread<LBMD_STORE_F16><<<blocks, threads, 0, s>>>(g, sp_node, sp_w, J, nw, (__half *)dst, bump);
+      k_spread<LBMD_STORE_F16><<<blocks, threads, 0, s>>>(g, sp_node, sp_w, J, nw, (__half *)dst, mode, bump);
       break;
     case LBMD_STORE_BF16:
-      k_spread<LBMD_STORE_BF16><<<blocks, threads, 0, s>>>(g, sp_node, sp_w, J, nw, (__nv_bfloat16 *)dst, bump);
+      k_spread<LBMD_STORE_BF16><<<blocks, threads, 0, s>>>(g, sp_node, sp_w, J, nw, (__nv_bfloat16 *)dst, mode, bump);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -20,6 +20,7 @@ RUNNING, TRANSLOCATED, RETRACTED, NAN, SHAKE_FAIL = range(5)
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 FORCING = {"paper": 0, "guo": 1}
 COUPLING = {"trilinear": 0, "ngp": 1}
+STREAMING = {"pull": 0, "aa": 1}
 MAX_BEADS = 1024
 
 # names of the parameter dict (shared with the oracle's wrapper and the
@@ -33,7 +34,7 @@ DEFAULTS = dict(
     bead_mass=1.0, gamma=0.1, kT=1e-4, lj_sigma=1.8, lj_eps=1.0,
     kappa_phi=0.0, f_drive=0.02, bond_len=1.2,
     shake_tol=1e-6, shake_max_iter=12, init_tg_amp=0.0, seed=0, hydrodynamics=1,
-    diag_every=0, diag_capacity=0, kT_fluid=0.0,
+    diag_every=0, diag_capacity=0, kT_fluid=0.0, streaming="pull",
 )
 IGNORED_KEYS = {"bonds"}  # oracle-only keys
 
@@ -47,6 +48,7 @@ class lbmd_params(C.Structure):
         ("coupling", C.c_int32), ("n_beads", C.c_int32), ("md_substeps", C.c_int32),
         ("n_constraints", C.c_int32), ("shake_max_iter", C.c_int32),
         ("solvent_free", C.c_int32), ("diag_every", C.c_int32), ("diag_capacity", C.c_int32),
+        ("streaming", C.c_int32),
         ("tau", C.c_double), ("rho0", C.c_double), ("body_force", C.c_double * 3),
         ("bead_mass", C.c_double), ("gamma", C.c_double), ("kT", C.c_double),
         ("lj_sigma", C.c_double), ("lj_eps", C.c_double), ("kappa_phi", C.c_double),
@@ -170,6 +172,7 @@ def make_params(p: dict, init_pos=None, init_vel=None, init_rho=None, init_u=Non
     cp.storage = STORAGE[p["storage"]]
     cp.forcing = FORCING[p["forcing"]]
     cp.coupling = COUPLING[p["coupling"]]
+    cp.streaming = STREAMING[p["streaming"]]
     for k in ("tau", "rho0", "bead_mass", "gamma", "kT", "lj_sigma", "lj_eps", "kappa_phi",
               "f_drive", "shake_tol", "init_tg_amp", "kT_fluid"):
         setattr(cp, k, float(p[k]))

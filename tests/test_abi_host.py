@@ -51,6 +51,26 @@ def test_workspace_covers_two_population_buffers():
         assert base <= n <= base + 80 * 2 ** 20
 
 
+def test_inplace_streaming_keeps_one_population_buffer():
+    pos = np.zeros((400, 3)) + 130.0
+    for storage, es in (("f32", 4), ("f16", 2)):
+        p = dict(si.paper_translocation(0), storage=storage)
+        pull = _ws(p, init_pos=pos)
+        aa = _ws(dict(p, streaming="aa"), init_pos=pos)
+        Vp = 256 * 128 * 128  # already a multiple of 64
+        assert pull - aa == 19 * Vp * es
+
+
+def test_unknown_streaming_rejected():
+    p = si.small_translocation(0, n_beads=4)
+    pos = si.saw_chain(p, 0)
+    cp, keep = lb.make_params(p, init_pos=pos)
+    cp.streaming = 7
+    with pytest.raises(lb.LbmdError) as e:
+        lb.lbmd_workspace_size(cp)
+    assert e.value.code == lb.lbmd.LBMD_EINVAL and "streaming" in str(e.value)
+
+
 @pytest.mark.parametrize("bad,msg", [
     (dict(tau=0.5), "tau"),
     (dict(nx=0), "box"),
@@ -122,6 +142,7 @@ def test_ensemble_workspace_holds_every_member():
     (lambda m: m[1].update(storage="f16"), lb.lbmd.LBMD_EUNSUPPORTED),
     (lambda m: m[2].update(forcing="guo"), lb.lbmd.LBMD_EUNSUPPORTED),
     (lambda m: m[0].update(tau=0.4), lb.lbmd.LBMD_EINVAL),
+    (lambda m: m[1].update(streaming="aa"), lb.lbmd.LBMD_EUNSUPPORTED),
 ])
 def test_ensemble_rejects_mixed_or_bad_members(change, code):
     members, starts = si.ragged_ensemble(3, seed=4)
