@@ -205,6 +205,35 @@ int lbmd_read_populations(lbmd_ctx *ctx, float *f, int dst_is_device);
  */
 int lbmd_read_beads(lbmd_ctx *ctx, double *pos, double *vel, int dst_is_device);
 
+/* Status word at the start of the block of lbmd_read_beads_async (fields as
+ * lbmd_status). */
+typedef struct lbmd_status_word {
+  int64_t step;        /* LB steps completed                               */
+  int64_t t_transloc;  /* first step with N_T = N, -1 before               */
+  int32_t n_trans;     /* N_T                                              */
+  int32_t state;       /* LBMD_RUNNING, ...                                */
+} lbmd_status_word;
+
+/* Bytes of the block of lbmd_read_beads_async for n_beads beads. */
+#define LBMD_BEAD_BLOCK_BYTES(n_beads) (32 + 48 * (size_t)(n_beads))
+
+/*
+ * Asynchronous host read-out for pipelined loops: enqueues on the context's
+ * stream one kernel and one copy that fill `dst` (caller-owned page-locked
+ * host memory: cudaHostAlloc / cudaHostRegister) with
+ *   offset 0:            lbmd_status_word,
+ *   offset 32:           unwrapped positions, 3*n_beads doubles [i][xyz],
+ *   offset 32 + 24 n:    velocities, 3*n_beads doubles,
+ * LBMD_BEAD_BLOCK_BYTES(n_beads) bytes in all.  Nothing is synchronised: the
+ * block is valid once the stream has passed this point (synchronise it, or an
+ * event recorded on it after this call).  A following lbmd_step may be
+ * enqueued at once; its kernels run after the copy.  With pageable memory the
+ * call may block until the copy is done.  Uses the context's read-out staging;
+ * read-outs enqueued later on the stream do not disturb it.
+ * Errors: LBMD_EINVAL (dst NULL or bytes too small), LBMD_ECUDA.
+ */
+int lbmd_read_beads_async(lbmd_ctx *ctx, void *dst, size_t bytes);
+
 /*
  * Of the last step: the fluid velocity interpolated at each bead, u_i, and the
  * impulse J_i = sum over substeps of Delta t_MD (F_drag + F_r) that was handed

@@ -294,27 +294,30 @@ int lbmd_step(lbmd_ctx *c, int64_t n_steps) {
   if (n_steps < 0) return fail(LBMD_EINVAL, "n_steps < 0");
   if (n_steps == 0) return LBMD_OK;
   c->status_fresh = 0;
-  CK(c, cudaEventRecord(c->ev_in, c->user));
-  CK(c, cudaStreamWaitEvent(c->own, c->ev_in, 0));
   if (c->timing) {
+    // direct launches on the private streams, joined back into the caller's
+    CK(c, cudaEventRecord(c->ev_in, c->user));
+    CK(c, cudaStreamWaitEvent(c->own, c->ev_in, 0));
     for (int64_t k = 0; k < n_steps; ++k) {
       CK(c, enqueue_step(c, c->cur));
       c->cur ^= 1;
     }
-  } else {
-    int64_t left = n_steps;
-    for (int gi = 2; gi >= 0; --gi) {
-      const int len = kGraphSteps[gi];
-      while (left >= len) {
-        if (!c->graph[c->cur][gi]) CK(c, capture(c, c->cur, len, &c->graph[c->cur][gi]));
-        CK(c, cudaGraphLaunch(c->graph[c->cur][gi], c->own));
-        if (len & 1) c->cur ^= 1;
-        left -= len;
-      }
+    CK(c, cudaEventRecord(c->ev_out, c->own));
+    CK(c, cudaStreamWaitEvent(c->user, c->ev_out, 0));
+    return LBMD_OK;
+  }
+  // graphs (captured on the private streams) launch straight into the
+  // caller's stream: no cross-stream handshake per call
+  int64_t left = n_steps;
+  for (int gi = 2; gi >= 0; --gi) {
+    const int len = kGraphSteps[gi];
+    while (left >= len) {
+      if (!c->graph[c->cur][gi]) CK(c, capture(c, c->cur, len, &c->graph[c->cur][gi]));
+      CK(c, cudaGraphLaunch(c->graph[c->cur][gi], c->user));
+      if (len & 1) c->cur ^= 1;
+      left -= len;
     }
   }
-  CK(c, cudaEventRecord(c->ev_out, c->own));
-  CK(c, cudaStreamWaitEvent(c->user, c->ev_out, 0));
   return LBMD_OK;
 }
 
@@ -429,6 +432,17 @@ int lbmd_read_beads(lbmd_ctx *c, double *pos, double *vel, int dst_is_device) {
   return read_bead_pair(c, pos, vel, dst_is_device, false);
 }
 
+int lbmd_read_beads_async(lbmd_ctx *c, void *dst, size_t bytes) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  const size_t need = kBeadBlockHeader + 48 * (size_t)c->N;
+  if (!dst || bytes < need) return fail(LBMD_EINVAL, "dst is NULL or smaller than %zu bytes", need);
+  // one kernel fills the block in the staging buffer, one copy moves it
+  CK(c, launch_bead_block(c->chain, c->status, c->stage, c->user));
+  CK(c, cudaMemcpyAsync(dst, c->stage, need, cudaMemcpyDeviceToHost, c->user));
+  return LBMD_OK;
+}
+
 int lbmd_read_bead_aux(lbmd_ctx *c, double *u_i, double *impulse, int dst_is_device) {
   return read_bead_pair(c, u_i, impulse, dst_is_device, true);
 }
@@ -520,6 +534,7 @@ int lbmd_read_diagnostics(lbmd_ctx *c, lbmd_diag *records, int32_t max_records,
 
 int lbmd_destroy(lbmd_ctx *c) {
   if (!c) return LBMD_OK;
+  cudaStreamSynchronize(c->user);
   cudaStreamSynchronize(c->own);
   cudaStreamSynchronize(c->side);
   destroy_ctx(c);

@@ -39,7 +39,8 @@ long long chunk_cells_for(const lbmd_params &p) {
 
 size_t stage_floats_for(const lbmd_params &p) {
   const size_t Np = (size_t)std::max(p.n_beads, 1);
-  return std::max((size_t)19 * (size_t)chunk_cells_for(p), (size_t)6 * Np * 2);
+  // 19 populations of a chunk, or 6 N doubles of bead read-out plus a status word
+  return std::max((size_t)19 * (size_t)chunk_cells_for(p), (size_t)6 * Np * 2 + 8);
 }
 
 Layout make_layout(const lbmd_params &p, bool with_stage) {

@@ -220,6 +220,9 @@ cudaError_t launch_ens_spread(int storage, const EnsMember *mem, const int2 *bea
 
 cudaError_t launch_read_beads(const float4 *pos, const float4 *pos_lo, const float4 *vel, int N,
                               int ox, int oy, int oz, double *dpos, double *dvel, cudaStream_t s);
+// The block of lbmd_read_beads_async into device memory `out` (32 + 48 N bytes).
+constexpr size_t kBeadBlockHeader = 32;
+cudaError_t launch_bead_block(const ChainArgs &a, const DevStatus *st, void *out, cudaStream_t s);
 cudaError_t launch_read_bead_aux(const float4 *ui, const float4 *J, int N, double *dui,
                                  double *dJ, cudaStream_t s);
 

@@ -1071,6 +1071,36 @@ cudaError_t launch_read_beads(const float4 *pos, const float4 *pos_lo, const flo
   return cudaGetLastError();
 }
 
+// The block of lbmd_read_beads_async: the status word at offset 0, then the
+// unwrapped positions and the velocities (3N doubles each) from offset 32.
+__global__ void k_bead_block(const float4 *pos, const float4 *pos_lo, const float4 *vel, int N,
+                             int ox, int oy, int oz, const DevStatus *st, char *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    lbmd_status_word *w = (lbmd_status_word *)out;
+    w->step = st->step;
+    w->t_transloc = st->t_transloc;
+    w->n_trans = st->n_trans;
+    w->state = st->state;
+  }
+  if (i >= N) return;
+  double *dpos = (double *)(out + kBeadBlockHeader), *dvel = dpos + 3 * (size_t)N;
+  const float4 r = pos[i], l = pos_lo[i], v = vel[i];
+  dpos[3 * i] = (double)ox + (double)r.x + (double)l.x;
+  dpos[3 * i + 1] = (double)oy + (double)r.y + (double)l.y;
+  dpos[3 * i + 2] = (double)oz + (double)r.z + (double)l.z;
+  dvel[3 * i] = v.x;
+  dvel[3 * i + 1] = v.y;
+  dvel[3 * i + 2] = v.z;
+}
+
+cudaError_t launch_bead_block(const ChainArgs &a, const DevStatus *st, void *out, cudaStream_t s) {
+  const int n = a.N > 0 ? a.N : 1;
+  k_bead_block<<<(n + 255) / 256, 256, 0, s>>>(a.pos, a.pos_lo, a.vel, a.N, a.ox, a.oy, a.oz, st,
+                                               (char *)out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_read_bead_aux(const float4 *ui, const float4 *J, int N, double *dui,
                                  double *dJ, cudaStream_t s) {
   if (N <= 0) return cudaSuccess;

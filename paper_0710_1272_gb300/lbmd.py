@@ -60,6 +60,11 @@ class lbmd_params(C.Structure):
     ]
 
 
+class lbmd_status_word(C.Structure):
+    _fields_ = [("step", C.c_int64), ("t_transloc", C.c_int64), ("n_trans", C.c_int32),
+                ("state", C.c_int32)]
+
+
 class lbmd_diag(C.Structure):
     _fields_ = [("step", C.c_int64), ("n_trans", C.c_int32), ("reserved", C.c_int32),
                 ("r_u", C.c_double), ("r_t", C.c_double), ("r_e", C.c_double),
@@ -107,6 +112,7 @@ def load(build_if_missing: bool = True):
     L.lbmd_read_populations.argtypes = [P, P, C.c_int]
     L.lbmd_read_beads.argtypes = [P, P, P, C.c_int]
     L.lbmd_read_bead_aux.argtypes = [P, P, P, C.c_int]
+    L.lbmd_read_beads_async.argtypes = [P, P, C.c_size_t]
     L.lbmd_status.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                               C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
     L.lbmd_solver_stats.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
@@ -138,6 +144,7 @@ def load(build_if_missing: bool = True):
     L.lbmd_last_message.restype = C.c_char_p
     for name in ("lbmd_workspace_size", "lbmd_create", "lbmd_step", "lbmd_read_fields",
                  "lbmd_read_populations", "lbmd_read_beads", "lbmd_read_bead_aux", "lbmd_status",
+                 "lbmd_read_beads_async",
                  "lbmd_set_kernel_timing", "lbmd_lb_kernel_time", "lbmd_destroy", "lbmd_version",
                  "lbmd_solver_stats", "lbmd_kernel_times", "lbmd_lb_step_noalloc",
                  "lbmd_read_diagnostics", "lbmd_ensemble_read_diagnostics", *ENSEMBLE_FUNCTIONS):
@@ -236,6 +243,26 @@ def lbmd_read_populations(ctx, f_ptr, dst_is_device: int) -> None:
 
 def lbmd_read_beads(ctx, pos_ptr, vel_ptr, dst_is_device: int) -> None:
     _check(load().lbmd_read_beads(ctx, pos_ptr, vel_ptr, dst_is_device), "lbmd_read_beads")
+
+
+def bead_block_bytes(n_beads: int) -> int:
+    """Bytes of the block lbmd_read_beads_async writes (LBMD_BEAD_BLOCK_BYTES)."""
+    return 32 + 48 * int(n_beads)
+
+
+def lbmd_read_beads_async(ctx, dst_ptr, nbytes: int) -> None:
+    """Enqueue the status word, positions and velocities into page-locked host
+    memory at ``dst_ptr`` (layout of LBMD_BEAD_BLOCK_BYTES); no synchronisation."""
+    _check(load().lbmd_read_beads_async(ctx, dst_ptr, int(nbytes)), "lbmd_read_beads_async")
+
+
+def decode_bead_block(block: np.ndarray, n_beads: int):
+    """(status dict, positions (N, 3), velocities (N, 3)) of a uint8 block."""
+    b = np.asarray(block, dtype=np.uint8)
+    w = lbmd_status_word.from_buffer_copy(b[:C.sizeof(lbmd_status_word)].tobytes())
+    d = b[32:32 + 48 * n_beads].view(np.float64)
+    status = dict(step=w.step, n_trans=w.n_trans, state=w.state, t_transloc=w.t_transloc)
+    return status, d[:3 * n_beads].reshape(n_beads, 3), d[3 * n_beads:].reshape(n_beads, 3)
 
 
 def lbmd_read_bead_aux(ctx, ui_ptr, j_ptr, dst_is_device: int) -> None:
