@@ -318,6 +318,10 @@ def run_ours(args):
         status, pos_k, _ = lb.decode_bead_block(blocks[k % 2].numpy(), N)
         assert status["step"] == step0 + k + 1 and np.isfinite(pos_k).all()
 
+    # the one-step graphs of both step parities exist before the timed loop
+    lb.lbmd_step(sim.ctx, 1)
+    lb.lbmd_step(sim.ctx, 1)
+    step0 += 2
     barrier()
     t0 = time.perf_counter()
     for k in range(e2e_steps):

@@ -83,8 +83,18 @@ __device__ __forceinline__ M2 mmul(M2 x, M2 y) {
             x.c * y.b + x.d * y.d};
 }
 __device__ __forceinline__ M2 madd(M2 x, M2 y) { return M2{x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d}; }
+
+// Hardware reciprocal approximation (relative error ~2^-23) for the
+// tridiagonal solves: they are latency-bound chains, and a correctly rounded
+// reciprocal costs several dependent instructions.
+__device__ __forceinline__ float rcp_fast(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ M2 minv(M2 x) {
-  const float r = __frcp_rn(x.a * x.d - x.b * x.c);
+  const float r = rcp_fast(x.a * x.d - x.b * x.c);
   return M2{x.d * r, -x.b * r, -x.c * r, x.a * r};
 }
 __device__ __forceinline__ M2 mshfl_up(M2 x, int s) {
@@ -131,8 +141,8 @@ __device__ float spike_tri_solve(int n, float a, float b, float c, float d, floa
     const float r0p = __shfl_down_sync(0xffffffffu, r0, s), r1p = __shfl_down_sync(0xffffffffu, r1, s);
     const float r2p = __shfl_down_sync(0xffffffffu, r2, s);
     const bool hm = lane >= s, hp = lane + s < 32;
-    const float k1 = hm ? al * __frcp_rn(bm) : 0.f;
-    const float k2 = hp ? ga * __frcp_rn(bp) : 0.f;
+    const float k1 = hm ? al * rcp_fast(bm) : 0.f;
+    const float k2 = hp ? ga * rcp_fast(bp) : 0.f;
     const float nal = hm ? -k1 * am : 0.f, nga = hp ? -k2 * gp : 0.f;
     be = be - k1 * gm - k2 * ap;
     r0 = r0 - k1 * r0m - k2 * r0p;
@@ -141,7 +151,7 @@ __device__ float spike_tri_solve(int n, float a, float b, float c, float d, floa
     al = nal;
     ga = nga;
   }
-  const float ib = 1.0f / be;
+  const float ib = rcp_fast(be);
   const float y = r0 * ib, v = r1 * ib, sw = r2 * ib;
   if (nch > 1) {
     if (lane == 0 && w < nch) {
