@@ -39,9 +39,23 @@ __device__ __forceinline__ float dot(F3 a, F3 b) { return a.x * b.x + a.y * b.y 
 int md_threads(int N) { return (N + 31) / 32 * 32; }
 
 // Shared memory of the MD block: positions (hi, lo), displacements, bond
-// vectors, velocities, the tridiagonal work arrays and the pair lists.
+// vectors, velocities, the tridiagonal work arrays, the pair lists and, for
+// chains of up to 512 beads, up to 32 solid nodes of each bead's wall list as
+// integer coordinates of the chain's local frame (longer wall lists are read
+// from the workspace).
+constexpr int kWallShared = 32;
+constexpr int kWallSharedMaxN = 512;
+
+// Bytes before the shared wall lists, rounded up to 16 (the short4 entries
+// need 8-byte alignment; 180 N bytes is not a multiple of 8 for odd N).
+__host__ __device__ inline size_t md_smem_head(int N) {
+  const size_t head = (size_t)N * (5 * sizeof(float4) + sizeof(float) + kMaxPairs * sizeof(short));
+  return (head + 15) / 16 * 16;
+}
+
 size_t md_smem_bytes(int N) {
-  return (size_t)N * (5 * sizeof(float4) + sizeof(float) + kMaxPairs * sizeof(short));
+  const size_t walls = N <= kWallSharedMaxN ? (size_t)N * kWallShared * sizeof(short4) : 0;
+  return md_smem_head(N) + walls;
 }
 
 // Double-float helpers: a coordinate is hi + lo with |lo| <= ulp(hi) / 2.
@@ -379,10 +393,11 @@ __device__ __forceinline__ void wall_add(float4 rh, float4 rl, float4 node, floa
 }
 
 // Bead i's pair forces from its shared-memory list and wall forces from its
-// solid-node list.
+// solid-node list: the shared-memory copy SW (column i, entry q at SW[q N])
+// when nws >= 0, else the workspace list.
 __device__ __forceinline__ F3 list_forces(const ChainArgs &a, int i, float4 rh, float4 rl,
                                           const float4 *s_rh, const float4 *s_rl,
-                                          const short *L, int np) {
+                                          const short *L, int np, const short4 *SW, int nws) {
   const LbGeom &g = a.geo;
   const float sig2 = a.sigma * a.sigma;
   const float rc = kTwoSixth * a.sigma, rc2 = rc * rc;
@@ -398,6 +413,14 @@ __device__ __forceinline__ F3 list_forces(const ChainArgs &a, int i, float4 rh, 
     d.z -= Lz * rintf(d.z * iLz);
     wca_add(d, sig2, rc2, eps24, F);
   }
+  if (nws >= 0) {
+#pragma unroll 4
+    for (int q = 0; q < nws; ++q) {
+      const short4 w = SW[q * a.N];
+      wall_add(rh, rl, make_float4((float)w.x, (float)w.y, (float)w.z, 0.f), sig2, rc2, eps24, F);
+    }
+    return F;
+  }
   const int nw = a.wl_cnt[i];
   const float4 *W = a.wl_list + (size_t)i * kMaxWall;
 #pragma unroll 4
@@ -405,11 +428,20 @@ __device__ __forceinline__ F3 list_forces(const ChainArgs &a, int i, float4 rh, 
   return F;
 }
 
+// A wall node's local coordinates fit the shared-memory entry.
+__device__ __forceinline__ bool fits_short(float4 n) {
+  return fabsf(n.x) <= 32000.f && fabsf(n.y) <= 32000.f && fabsf(n.z) <= 32000.f;
+}
+
 // Rebuild bead i's lists with cutoff r_c + skin: pair list (shared memory,
 // column i, entry q at L[q N]; copied to the workspace for the next launch)
-// and solid-node list (workspace).  Returns the pair count, or -1 on overflow.
+// and solid-node list (workspace, and its shared copy SW when not null and
+// it fits: *nws = its length, else -1).  Solid nodes are kept within the
+// sphere of radius r_c + skin (a node beyond it exerts no force while the
+// bead stays within half the skin of the build position).  Returns the pair
+// count, or -1 on overflow.
 __device__ int build_lists(const ChainArgs &a, int i, float4 rh, float4 rl, const float4 *s_rh,
-                           const float4 *s_rl, short *L) {
+                           const float4 *s_rl, short *L, short4 *SW, int *nws) {
   const LbGeom &g = a.geo;
   const int N = a.N;
   const float rlist = kTwoSixth * a.sigma + kSkin, rl2 = rlist * rlist;
@@ -434,10 +466,18 @@ __device__ int build_lists(const ChainArgs &a, int i, float4 rh, float4 rl, cons
   }
   float4 *W = a.wl_list + (size_t)i * kMaxWall;
   int nw = 0;
+  bool packed = SW != nullptr;
   for_solid_nodes(a, rh, rl, rlist, [&](float4 node) {
+    const F3 d{(rh.x - node.x) + rl.x, (rh.y - node.y) + rl.y, (rh.z - node.z) + rl.z};
+    if (!(dot(d, d) < rl2)) return;
     if (nw < kMaxWall) W[nw] = node;
+    if (packed && nw < kWallShared && fits_short(node))
+      SW[nw * N] = make_short4((short)node.x, (short)node.y, (short)node.z, 0);
+    else
+      packed = false;
     ++nw;
   });
+  *nws = packed ? nw : -1;
   a.nl_cnt[i] = min(np, kMaxPairs);
   a.wl_cnt[i] = min(nw, kMaxWall);
   a.nl_ref[i] = rh;
@@ -456,6 +496,7 @@ __device__ F3 wall_stencil_forces(const ChainArgs &a, float4 rh, float4 rl) {
 
 // (2) the M MD substeps of one chain, one thread per bead, and (5) the
 // bookkeeping; `a` may live in parameter or shared memory.
+template <bool WS>
 __device__ __forceinline__ void md_cycle_body(const ChainArgs &a) {
   extern __shared__ float4 smem4[];
   const int N = a.N;
@@ -468,6 +509,9 @@ __device__ __forceinline__ void md_cycle_body(const ChainArgs &a) {
   float4 *s_v = s_b + N;      // velocities (RATTLE)
   float *s_lam = (float *)(s_v + N);  // N: SHAKE multipliers of the last substep
   short *s_nl = (short *)(s_lam + N);  // [kMaxPairs][N] pair lists, column per bead
+  // [kWallShared][N] wall lists, column per bead (WS: chains of <= 512 beads)
+  short4 *s_w = WS ? (short4 *)((char *)smem4 + md_smem_head(N)) : nullptr;
+  int nws = -1;  // length of this bead's shared wall list, -1: read the workspace
 
   const long long step = a.status->step;
   int nl_ok = a.status->nl_ok && a.status->nl_builds > 0;
@@ -487,6 +531,21 @@ __device__ __forceinline__ void md_cycle_body(const ChainArgs &a) {
       np = a.nl_cnt[i];
       const short *G = a.nl_list + (size_t)i * kMaxPairs;
       for (int q = 0; q < np; ++q) s_nl[q * N + i] = G[q];
+      if (WS) {
+        // this launch's substeps read the wall list from shared memory
+        const int nw = a.wl_cnt[i];
+        if (nw <= kWallShared) {
+          const float4 *W = a.wl_list + (size_t)i * kMaxWall;
+          bool fit = true;
+#pragma unroll 4
+          for (int q = 0; q < nw; ++q) {
+            const float4 node = W[q];
+            fit = fit && fits_short(node);
+            s_w[q * N + i] = make_short4((short)node.x, (short)node.y, (short)node.z, 0);
+          }
+          nws = fit ? nw : -1;
+        }
+      }
     }
   }
   const float half_skin2 = 0.25f * kSkin * kSkin;
@@ -507,7 +566,7 @@ __device__ __forceinline__ void md_cycle_body(const ChainArgs &a) {
       // neighbour lists: pairs and solid nodes within r_c + skin
       int cnt = 0;
       if (bead) {
-        cnt = build_lists(a, i, rh, rl, s_rh, s_rl, s_nl + i);
+        cnt = build_lists(a, i, rh, rl, s_rh, s_rl, s_nl + i, WS ? s_w + i : nullptr, &nws);
         ref = rh;
       }
       nl_ok = __syncthreads_and(cnt >= 0);
@@ -519,7 +578,8 @@ __device__ __forceinline__ void md_cycle_body(const ChainArgs &a) {
       F3 Fc = bend_drive_forces(a, i, s_rh, s_rl);
       if (a.eps != 0.f) {
         if (nl_ok)
-          Fc = Fc + list_forces(a, i, rh, rl, s_rh, s_rl, s_nl + i, np);
+          Fc = Fc + list_forces(a, i, rh, rl, s_rh, s_rl, s_nl + i, np, WS ? s_w + i : nullptr,
+                                WS ? nws : -1);
         else
           Fc = Fc + all_pair_forces(a, i, rh, rl, s_rh, s_rl) + wall_stencil_forces(a, rh, rl);
       }
@@ -709,7 +769,7 @@ __device__ __forceinline__ void md_cycle_body(const ChainArgs &a) {
 
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_md_cycle(ChainArgs a) {
-  md_cycle_body(a);
+  md_cycle_body<BLOCK <= kWallSharedMaxN>(a);
 }
 
 // Ensemble variant: block b runs chain chains[b] if its realisation is live.
@@ -726,7 +786,7 @@ __global__ void __launch_bounds__(BLOCK)
   int *dst = reinterpret_cast<int *>(&s_a);
   for (int k = threadIdx.x; k < (int)(sizeof(ChainArgs) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
   __syncthreads();
-  md_cycle_body(s_a);
+  md_cycle_body<BLOCK <= kWallSharedMaxN>(s_a);
 }
 
 // Stage (1) for (bead, corner) pair e = 8 i + k handled by one thread; the
@@ -828,12 +888,12 @@ __global__ void __launch_bounds__(256)
 }
 
 cudaError_t md_prepare() {
-  const int smem = (int)md_smem_bytes(LBMD_MAX_BEADS);
+  const int s512 = (int)md_smem_bytes(kWallSharedMaxN), s1024 = (int)md_smem_bytes(LBMD_MAX_BEADS);
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_md_cycle<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_md_cycle<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_ens_md_cycle<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_ens_md_cycle<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if ((e = cudaFuncSetAttribute(k_md_cycle<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, s512)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_md_cycle<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1024)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_ens_md_cycle<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, s512)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_ens_md_cycle<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1024);
 }
 
 cudaError_t launch_gather(int storage, const ChainArgs &a, cudaStream_t s) {
