@@ -64,7 +64,6 @@ Layout make_layout(const lbmd_params &p, bool with_stage) {
   L.solid = take(rows * L.ntx * sizeof(uint32_t));
   L.tile = take(rows * L.ntx);
   L.lmask = take((size_t)V * sizeof(uint32_t));
-  L.xslab = take((size_t)p.nx);
   L.pos = take(Np * sizeof(float4));
   L.pos_lo = take(Np * sizeof(float4));
   L.vel = take(Np * sizeof(float4));
@@ -180,7 +179,6 @@ namespace {
 struct HostGeometry {
   std::vector<uint32_t> bits;   // [nz][ny][ntx]
   std::vector<uint8_t> tile;    // [nz][ny][ntx]
-  std::vector<uint8_t> xslab;   // [nx]
 };
 
 }  // namespace
@@ -189,7 +187,6 @@ static void build_geometry(const lbmd_params &p, int ntx, HostGeometry &G) {
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   G.bits.assign((size_t)nz * ny * ntx, 0u);
   G.tile.assign((size_t)nz * ny * ntx, 0u);
-  G.xslab.assign((size_t)nx, 0u);
   const bool any_solid = p.y_walls || p.wall_x >= 0;
   if (!any_solid) return;
   for (int z = 0; z < nz; ++z)
@@ -197,7 +194,6 @@ static void build_geometry(const lbmd_params &p, int ntx, HostGeometry &G) {
       for (int x = 0; x < nx; ++x)
         if (is_solid(p, x, y, z)) {
           G.bits[((size_t)z * ny + y) * ntx + (x >> 5)] |= 1u << (x & 31);
-          G.xslab[x] = 1;
         }
   std::vector<uint8_t> col((size_t)nx);
   for (int z = 0; z < nz; ++z)
@@ -286,7 +282,6 @@ cudaError_t init_instance(const lbmd_params &p, const Layout &L, char *ws, cudaS
   build_geometry(p, L.ntx, G);
   UP(cudaMemcpyAsync(ws + L.solid, G.bits.data(), G.bits.size() * 4, cudaMemcpyHostToDevice, s), "upload");
   UP(cudaMemcpyAsync(ws + L.tile, G.tile.data(), G.tile.size(), cudaMemcpyHostToDevice, s), "upload");
-  UP(cudaMemcpyAsync(ws + L.xslab, G.xslab.data(), G.xslab.size(), cudaMemcpyHostToDevice, s), "upload");
   UP(launch_link_mask(g, (uint32_t *)(ws + L.lmask), s), "link mask");
 
   out.phys.omega = (float)(1.0 / p.tau);
@@ -358,7 +353,6 @@ cudaError_t init_instance(const lbmd_params &p, const Layout &L, char *ws, cudaS
   UP(cudaMemcpyAsync(out.status, &st, sizeof(st), cudaMemcpyHostToDevice, s), "upload");
   ChainArgs &a = out.chain;
   a.geo = g;
-  a.xslab = (const uint8_t *)(ws + L.xslab);
   a.has_wall = p.wall_x >= 0;
   a.wall_x = p.wall_x;
   a.wall_t = p.wall_thickness;
@@ -367,6 +361,7 @@ cudaError_t init_instance(const lbmd_params &p, const Layout &L, char *ws, cudaS
   if (p.wall_x >= 0) pore_origin(p, y0, z0);
   a.pore_y0 = y0;
   a.pore_z0 = z0;
+  a.y_walls = p.y_walls;
   a.rho0 = (float)p.rho0;
   for (int k = 0; k < 3; ++k) a.g[k] = (float)p.body_force[k];
   a.forcing = p.forcing;

@@ -85,8 +85,7 @@ struct ChainArgs {
   LbGeom geo;
   const void *f;            // populations to gather from (kPop* layout f_mode)
   int f_mode;
-  const uint8_t *xslab;     // [nx]: 1 if the x-layer holds a solid node
-  int has_wall, wall_x, wall_t, pore_d, pore_y0, pore_z0;
+  int has_wall, wall_x, wall_t, pore_d, pore_y0, pore_z0, y_walls;  // Sec. III geometry
   float rho0, g[3];
   int forcing, coupling;
   int N, M, has_bonds, shake_maxit;

@@ -355,6 +355,22 @@ __device__ __forceinline__ void block_sum(float (&v)[K], float *red) {
   for (int k = 0; k < K; ++k) v[k] = red[32 * K + k];
 }
 
+// Solid node test from the Sec. III geometry itself (the wall layers
+// wall_x .. wall_x + wall_t - 1 minus the d x d pore, and the rows y = 0 and
+// y = ny - 1 with y-walls): the rule the solid bitfield is built from, with
+// no memory read.  Coordinates inside the box.
+__device__ __forceinline__ bool wall_layer(const ChainArgs &a, int x) {
+  int dx = x - a.wall_x;
+  if (dx < 0) dx += a.geo.nx;
+  return a.has_wall && dx < a.wall_t;
+}
+__device__ __forceinline__ bool solid_geom(const ChainArgs &a, int x, int y, int z) {
+  if (a.y_walls && (y == 0 || y == a.geo.ny - 1)) return true;
+  if (!wall_layer(a, x)) return false;
+  return !(a.pore_d > 0 && y >= a.pore_y0 && y < a.pore_y0 + a.pore_d && z >= a.pore_z0 &&
+           z < a.pore_z0 + a.pore_d);
+}
+
 // Solid nodes around a bead within `radius` (node offsets n with
 // |n - s| < radius per axis), visited in x, y, z order.  For each solid node
 // calls fn(node coordinate in the chain's local frame).
@@ -362,6 +378,7 @@ template <typename Fn>
 __device__ __forceinline__ void for_solid_nodes(const ChainArgs &a, float4 rh, float4 rl,
                                                 float radius, Fn fn) {
   const LbGeom &g = a.geo;
+  if (!a.has_wall && !a.y_walls) return;
   int c[3];
   float sf[3];
   cell_frac_hl(rh.x, rl.x, a.ox, g.nx, c[0], sf[0]);
@@ -372,13 +389,13 @@ __device__ __forceinline__ void for_solid_nodes(const ChainArgs &a, float4 rh, f
   const int lo1 = (int)ceilf(sf[1] - radius), hi1 = (int)floorf(sf[1] + radius);
   const int lo2 = (int)ceilf(sf[2] - radius), hi2 = (int)floorf(sf[2] + radius);
   for (int ox = lo0; ox <= hi0; ++ox) {
-    const int x = wrapi(c[0] + ox, g.nx);
-    if (!__ldg(&a.xslab[x])) continue;
+    const int x = wrap_near(c[0] + ox, g.nx);
+    if (!a.y_walls && !wall_layer(a, x)) continue;  // no solid node in this layer
     for (int oy = lo1; oy <= hi1; ++oy) {
-      const int y = wrapi(c[1] + oy, g.ny);
+      const int y = wrap_near(c[1] + oy, g.ny);
       for (int oz = lo2; oz <= hi2; ++oz) {
-        const int z = wrapi(c[2] + oz, g.nz);
-        if (!solid_at(g.solid, g.ntx, g.ny, x, y, z)) continue;
+        const int z = wrap_near(c[2] + oz, g.nz);
+        if (!solid_geom(a, x, y, z)) continue;
         fn(make_float4(fx + (float)ox, fy + (float)oy, fz + (float)oz, 0.f));
       }
     }
