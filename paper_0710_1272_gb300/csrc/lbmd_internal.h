@@ -183,6 +183,17 @@ cudaError_t launch_read_pulled(int storage, const LbGeom &g, float rho0, const v
                                long long fstride, cudaStream_t s);
 cudaError_t launch_gather(int storage, const ChainArgs &a, cudaStream_t s);
 cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s);
+// Two-phase spread of 16-bit storage through the per-node slots `force`
+// ({Fx, Fy, Fz, owner}, resting at {0, 0, 0, kOwnerFree}; every byte of the
+// owner 0x7f, so a strided memset prepares the field): accumulate (any
+// time after the MD cycle), then apply to `dst` in layout `mode` (after the
+// stream-collide).
+constexpr int kOwnerFree = 0x7f7f7f7f;
+cudaError_t launch_spread_accum(const int *sp_node, const float *sp_w, const float4 *J, int nw,
+                                float4 *force, cudaStream_t s);
+cudaError_t launch_spread_apply(int storage, const LbGeom &g, const int *sp_node, int nw,
+                                float4 *force, void *dst, int mode, DevStatus *bump,
+                                cudaStream_t s);
 // Spread into the post-collision populations of `dst`, held in layout `mode`.
 cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, const float *sp_w,
                           const float4 *J, int N, int nw, void *dst, int mode, DevStatus *bump,

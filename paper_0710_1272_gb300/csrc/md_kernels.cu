@@ -1007,6 +1007,98 @@ __global__ void k_spread(LbGeom g, const int *__restrict__ sp_node, const float 
   }
 }
 
+// Two-phase spread for 16-bit population storage.  A 16-bit atomic add per
+// population and corner is slow (neighbouring lanes hit the same words) and
+// rounds each increment to 16 bits before the add.  Instead:
+//  (a) k_spread_accum, right after the MD cycle (beside the stream-collide):
+//      every (bead, corner) adds its force -w_ik J_i to the node's float slot
+//      {Fx, Fy, Fz, owner} and claims the node with the smallest lane index
+//      (atomicMin on owner, which rests at kOwnerFree);
+//  (b) k_spread_apply, after the stream-collide: the owner of each node reads
+//      the summed force, resets the slot, and adds S_p = 3 w_p c_p . F to the
+//      node's post-collision populations (wherever layout `mode` keeps them)
+//      with one plain read-modify-write each: h* <- round16(h* + S_p).
+// Slots are left as they were found, so the field needs clearing only once.
+__global__ void __launch_bounds__(256) k_spread_accum(const int *__restrict__ sp_node,
+                                                      const float *__restrict__ sp_w,
+                                                      const float4 *__restrict__ J, int nw,
+                                                      float4 *force) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nw) return;
+  const int node = sp_node[e];
+  if (node < 0) return;
+  const float w = sp_w[e];
+  const float4 j = J[e >> 3];
+  float *f = reinterpret_cast<float *>(force + node);
+  atomicAdd(f + 0, -w * j.x);
+  atomicAdd(f + 1, -w * j.y);
+  atomicAdd(f + 2, -w * j.z);
+  atomicMin(reinterpret_cast<int *>(f + 3), e);
+}
+
+template <int S>
+__global__ void __launch_bounds__(256)
+    k_spread_apply(LbGeom g, const int *__restrict__ sp_node, int nw, float4 *force,
+                   typename Store<S>::T *dst, int mode, DevStatus *bump) {
+  using St = Store<S>;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bump != nullptr && e == 0) bump->step += 1;
+  if (e >= nw) return;
+  const int node = sp_node[e];
+  if (node < 0) return;
+  float4 *slot = force + node;
+  if (reinterpret_cast<const int *>(slot)[3] != e) return;  // not the owner
+  const float4 F = *slot;
+  *slot = make_float4(0.f, 0.f, 0.f, __int_as_float(kOwnerFree));
+  const size_t Vp = (size_t)g.Vp;
+  uint32_t bb = 0u;
+  int x = 0, y = 0, z = 0;
+  if (mode == kPopAALocal) {
+    x = node % g.nx;
+    const int yz = node / g.nx;
+    y = yz % g.ny;
+    z = yz / g.ny;
+    bb = __ldg(&g.lmask[node]);  // bit opp(p): x_k + c_p is solid
+  }
+#pragma unroll
+  for (int p = 1; p < kQ; ++p) {
+    const float cf = cx(p) * F.x + cy(p) * F.y + cz(p) * F.z;
+    size_t at;
+    if (mode == kPopAALocal) {
+      const size_t t = ((size_t)wrapi(z + cz(p), g.nz) * g.ny + wrapi(y + cy(p), g.ny)) * g.nx +
+                       wrapi(x + cx(p), g.nx);
+      at = ((bb >> opp(p)) & 1u) ? (size_t)opp(p) * Vp + node : (size_t)p * Vp + t;
+    } else {
+      at = (size_t)(mode == kPopAASwap ? opp(p) : p) * Vp + node;
+    }
+    St::store(dst + at, St::load_plain(dst + at) + 3.0f * wq(p) * cf);
+  }
+}
+
+cudaError_t launch_spread_accum(const int *sp_node, const float *sp_w, const float4 *J, int nw,
+                                float4 *force, cudaStream_t s) {
+  if (nw <= 0) return cudaSuccess;
+  k_spread_accum<<<(nw + 255) / 256, 256, 0, s>>>(sp_node, sp_w, J, nw, force);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spread_apply(int storage, const LbGeom &g, const int *sp_node, int nw,
+                                float4 *force, void *dst, int mode, DevStatus *bump,
+                                cudaStream_t s) {
+  const int blocks = nw > 0 ? (nw + 255) / 256 : 1;
+  switch (storage) {
+    case LBMD_STORE_F16:
+      k_spread_apply<LBMD_STORE_F16><<<blocks, 256, 0, s>>>(g, sp_node, nw, force, (__half *)dst, mode, bump);
+      break;
+    case LBMD_STORE_BF16:
+      k_spread_apply<LBMD_STORE_BF16><<<blocks, 256, 0, s>>>(g, sp_node, nw, force, (__nv_bfloat16 *)dst, mode, bump);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, const float *sp_w,
                           const float4 *J, int N, int nw, void *dst, int mode, DevStatus *bump,
                           cudaStream_t s) {
