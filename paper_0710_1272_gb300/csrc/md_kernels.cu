@@ -1060,18 +1060,25 @@ __global__ void __launch_bounds__(256)
     z = yz / g.ny;
     bb = __ldg(&g.lmask[node]);  // bit opp(p): x_k + c_p is solid
   }
+  // all 18 loads first, then the stores: the slots are distinct, and issuing
+  // the loads together takes one memory latency instead of eighteen
+  size_t at[kQ];
+  float hv[kQ];
 #pragma unroll
   for (int p = 1; p < kQ; ++p) {
-    const float cf = cx(p) * F.x + cy(p) * F.y + cz(p) * F.z;
-    size_t at;
     if (mode == kPopAALocal) {
       const size_t t = ((size_t)wrapi(z + cz(p), g.nz) * g.ny + wrapi(y + cy(p), g.ny)) * g.nx +
                        wrapi(x + cx(p), g.nx);
-      at = ((bb >> opp(p)) & 1u) ? (size_t)opp(p) * Vp + node : (size_t)p * Vp + t;
+      at[p] = ((bb >> opp(p)) & 1u) ? (size_t)opp(p) * Vp + node : (size_t)p * Vp + t;
     } else {
-      at = (size_t)(mode == kPopAASwap ? opp(p) : p) * Vp + node;
+      at[p] = (size_t)(mode == kPopAASwap ? opp(p) : p) * Vp + node;
     }
-    St::store(dst + at, St::load_plain(dst + at) + 3.0f * wq(p) * cf);
+    hv[p] = St::load_plain(dst + at[p]);
+  }
+#pragma unroll
+  for (int p = 1; p < kQ; ++p) {
+    const float cf = cx(p) * F.x + cy(p) * F.y + cz(p) * F.z;
+    St::store(dst + at[p], hv[p] + 3.0f * wq(p) * cf);
   }
 }
 
