@@ -295,6 +295,50 @@ def test_coupled_variants_10_steps(variant):
     assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < 2e-5
 
 
+def _solid_nodes_near(p, pos, radius):
+    """Largest number of solid nodes within `radius` of any bead (host count)."""
+    solid = si.solid_mask(p)
+    best = 0
+    for r in pos:
+        c = np.floor(r).astype(int)
+        cnt = 0
+        for o in np.ndindex(7, 7, 7):
+            n = c + np.array(o) - 3
+            d = r - n
+            if d @ d < radius * radius and solid[n[2] % p["nz"], n[1] % p["ny"], n[0] % p["nx"]]:
+                cnt += 1
+        best = max(best, cnt)
+    return best
+
+
+def test_coupled_chain_through_thick_wall():
+    """A straight 12-bead chain threaded through the pore of a five-layer wall:
+    beads inside the channel have 36 solid nodes within the list sphere, more
+    than the 32 the shared-memory wall list takes, so their forces come from
+    the workspace list."""
+    p, _ = small_case(1, lj_eps=PAPER_EPS, wall_x=14, wall_thickness=5, n_beads=12)
+    pos = np.array([[14.5 + 1.2 * k, 7.0, 7.0] for k in range(12)])
+    assert _solid_nodes_near(p, pos, 2 ** (1 / 6) * p["lj_sigma"] + 0.8) > 32
+    sim, orc = pair(p, init_pos=pos)
+    for n in (1, 9, 10):
+        sim.step(n)
+        orc.step(n)
+        assert rel_err(sim.populations(), orc.populations()) < 2e-5, n
+        assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < 2e-5, n
+
+
+def test_coupled_chain_beside_y_walls():
+    """A chain in an 8-node-high channel with solid rows y = 0 and y = 7 next to
+    a two-layer wall: list builds take the wall rows from the geometry."""
+    p, pos = small_case(1, lj_eps=PAPER_EPS, ny=8, y_walls=1, wall_thickness=2)
+    sim, orc = pair(p, init_pos=pos)
+    for n in (1, 9, 10):
+        sim.step(n)
+        orc.step(n)
+        assert rel_err(sim.populations(), orc.populations()) < 2e-5, n
+        assert np.abs(sim.beads()[0] - orc.beads()[0]).max() < 2e-5, n
+
+
 def test_free_beads_and_single_bead():
     lb = _gpu()
     p = dict(si.small_translocation(0, n_beads=5), lj_eps=0.5, kT=1e-3)
