@@ -91,6 +91,15 @@ def workload(seed: int, storage: str, args=None):
     return p
 
 
+def launches_per_step(p) -> int:
+    """Kernels of one coupled step: gather, MD cycle, stream-collide and spread
+    (16-bit storage: the spread in two kernels); without beads the
+    stream-collide alone, plus the step-count kernel with the thermal source."""
+    if p["n_beads"] > 0:
+        return 5 if p["storage"] != "f32" else 4
+    return 2 if p.get("kT_fluid", 0) > 0 else 1
+
+
 def workload_name(p) -> str:
     if p.get("kT_fluid", 0) > 0:
         q = dict(p)
@@ -391,7 +400,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": nbytes,
                 "api": ("lbmd_step(1) + lbmd_read_beads_async(pinned host block, double-buffered; "
                         "the host waits for and checks step k's block after enqueuing step k+1)")},
-        "gpu_launches": (4 if p["n_beads"] > 0 else (2 if p.get("kT_fluid", 0) > 0 else 1)) * args.steps,
+        "gpu_launches": launches_per_step(p) * args.steps,
         "clocks": clocks,
         "status": st,
     }
