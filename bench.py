@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["translocation", "solvent", "poiseuille"],
+    ap.add_argument("--workload", choices=["translocation", "small", "solvent", "poiseuille"],
                     default="translocation")
     ap.add_argument("--box", type=int, default=256, help="edge of the periodic solvent box")
     ap.add_argument("--tau", type=float, default=1.0)
@@ -80,6 +80,10 @@ def workload(seed: int, storage: str, args=None):
         p["init_tg_amp"] = 0.01
     elif kind == "poiseuille":
         p = si.poiseuille_channel(256, 128, 128, tau=args.tau, g=1e-6)
+    elif kind == "small":
+        # 32x16x16 box, 3x3 pore, 20 beads: launch-latency bound, L2-resident
+        p = si.small_translocation(seed)
+        p["tau"] = args.tau
     else:
         p = si.paper_translocation(seed)
         p["tau"] = args.tau if args is not None else 1.0
