@@ -944,6 +944,26 @@ cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, k_md_cycle<1024>, a);
 }
 
+// Sum of F over the lanes in `peers` (the lanes of the warp that hit the same
+// node), added in ascending lane order; lanes that do not `take` part get 0.
+// The loop runs as many rounds as the largest group of the warp has lanes.
+__device__ __forceinline__ F3 peer_sum(unsigned peers, bool take, F3 F) {
+  unsigned rest = take ? peers : 0u;
+  const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(rest));
+  F3 sum{0.f, 0.f, 0.f};
+  for (int r = 0; r < rounds; ++r) {
+    const int src = rest ? __ffs(rest) - 1 : 0;
+    const float vx = __shfl_sync(0xffffffffu, F.x, src);
+    const float vy = __shfl_sync(0xffffffffu, F.y, src);
+    const float vz = __shfl_sync(0xffffffffu, F.z, src);
+    if (rest) {
+      sum = sum + F3{vx, vy, vz};
+      rest &= rest - 1;
+    }
+  }
+  return sum;
+}
+
 // ---------------------------------------------------------------------------
 // (3) extrapolation of the forces: node x_k receives -w_ik J_i as the source
 // S_p = 3 w_p c_p . F (Eq. 10, reaction sign) added to the post-collision
@@ -972,14 +992,7 @@ __global__ void k_spread(LbGeom g, const int *__restrict__ sp_node, const float 
     }
   }
   const unsigned peers = __match_any_sync(0xffffffffu, node);
-  F3 sum{0.f, 0.f, 0.f};
-#pragma unroll 4
-  for (int l = 0; l < 32; ++l) {
-    const float vx = __shfl_sync(0xffffffffu, F.x, l);
-    const float vy = __shfl_sync(0xffffffffu, F.y, l);
-    const float vz = __shfl_sync(0xffffffffu, F.z, l);
-    if ((peers >> l) & 1u) sum = sum + F3{vx, vy, vz};
-  }
+  const F3 sum = peer_sum(peers, node >= 0, F);
   const int leader = __ffs(peers) - 1;
   if (node >= 0 && lane == leader) {
     using St = Store<S>;
@@ -1157,14 +1170,7 @@ __global__ void __launch_bounds__(256)
     }
   }
   const unsigned peers = __match_any_sync(0xffffffffu, node);
-  F3 sum{0.f, 0.f, 0.f};
-#pragma unroll 4
-  for (int l = 0; l < 32; ++l) {
-    const float vx = __shfl_sync(0xffffffffu, F.x, l);
-    const float vy = __shfl_sync(0xffffffffu, F.y, l);
-    const float vz = __shfl_sync(0xffffffffu, F.z, l);
-    if ((peers >> l) & 1u) sum = sum + F3{vx, vy, vz};
-  }
+  const F3 sum = peer_sum(peers, node >= 0, F);
   const int leader = __ffs(peers) - 1;
   if (node >= 0 && lane == leader) {
     const EnsMember &M = mem[mi.x];
