@@ -96,11 +96,12 @@ def workload(seed: int, storage: str, args=None):
 
 
 def launches_per_step(p) -> int:
-    """Kernels of one coupled step: gather, MD cycle, stream-collide and spread
-    (16-bit storage: the spread in two kernels); without beads the
-    stream-collide alone, plus the step-count kernel with the thermal source."""
+    """Kernels of one coupled step: gather, MD cycle, stream-collide and the
+    spread in two kernels (accumulate beside the stream-collide, apply after
+    it); without beads the stream-collide alone, plus the step-count kernel
+    with the thermal source."""
     if p["n_beads"] > 0:
-        return 5 if p["storage"] != "f32" else 4
+        return 5
     return 2 if p.get("kT_fluid", 0) > 0 else 1
 
 

@@ -453,6 +453,7 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
     EnsMember &M = e->hmem[m];
     memset(&M, 0, sizeof(M));
     M.a = e->inst[m].chain;
+    M.a.md_accum = 1;  // the MD blocks accumulate the spread (beside the stream-collide)
     M.a.f = nullptr;
     M.a.f_mode = kPopPull;
     M.ph = e->inst[m].phys;

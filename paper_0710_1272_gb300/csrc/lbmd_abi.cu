@@ -42,7 +42,6 @@ struct lbmd_ctx {
   double timed_ms[3];            // summed durations of stream-collide, MD, spread
   long long timed_count;
   DevStatus *status;
-  float4 *force;  // two-phase spread slots (16-bit storage), or null
   float *stage;
   // pinned host staging of the host bead read-outs (with the status word,
   // so that lbmd_status right after needs no second synchronisation)
@@ -102,8 +101,8 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     if (t[3] && (e = cudaEventRecord(t[3], c->own)) != cudaSuccess) return e;
     for (int k : {0, 1, 4})
       if (t[k] && (e = cudaEventRecord(t[k], c->own)) != cudaSuccess) return e;
-    if ((e = launch_spread(c->p.storage, c->geo, c->chain.sp_node, c->chain.sp_w, c->chain.J, c->N,
-                           8 * c->N, B, mode_out, c->status, c->own)) != cudaSuccess)
+    if ((e = launch_spread_apply(c->p.storage, c->geo, c->chain, B, mode_out, c->status, c->own)) !=
+        cudaSuccess)
       return e;
     if (t[5] && (e = cudaEventRecord(t[5], c->own)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -120,10 +119,8 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     if ((e = cudaStreamWaitEvent(c->side, c->ev_fork, 0)) != cudaSuccess) return e;
     if ((e = launch_md_cycle(a, c->prio_high, c->side)) != cudaSuccess) return e;
     if (t[3] && (e = cudaEventRecord(t[3], c->side)) != cudaSuccess) return e;
-    if (c->force &&
-        (e = launch_spread_accum(c->chain.sp_node, c->chain.sp_w, c->chain.J, 8 * c->N, c->force,
-                                 c->side)) != cudaSuccess)
-      return e;
+    // accumulate part of the spread, beside the stream-collide
+    if ((e = launch_spread_accum(c->chain, c->side)) != cudaSuccess) return e;
   } else if (t[2]) {
     if ((e = cudaEventRecord(t[2], c->own)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(t[3], c->own)) != cudaSuccess) return e;
@@ -147,11 +144,9 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     if ((e = cudaEventRecord(c->ev_join, c->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(c->own, c->ev_join, 0)) != cudaSuccess) return e;
     if (t[4] && (e = cudaEventRecord(t[4], c->own)) != cudaSuccess) return e;
-    e = c->force ? launch_spread_apply(c->p.storage, c->geo, c->chain.sp_node, 8 * c->N, c->force, B,
-                                       mode_out, c->status, c->own)
-                 : launch_spread(c->p.storage, c->geo, c->chain.sp_node, c->chain.sp_w, c->chain.J,
-                                 c->N, 8 * c->N, B, mode_out, c->status, c->own);
-    if (e != cudaSuccess) return e;
+    if ((e = launch_spread_apply(c->p.storage, c->geo, c->chain, B, mode_out, c->status, c->own)) !=
+        cudaSuccess)
+      return e;
     if (t[5] && (e = cudaEventRecord(t[5], c->own)) != cudaSuccess) return e;
   } else if (t[4]) {
     if ((e = cudaEventRecord(t[4], c->own)) != cudaSuccess) return e;
@@ -285,7 +280,6 @@ int lbmd_create(const lbmd_params *params, void *dev_workspace, size_t bytes, vo
   c->geo = in.geo;
   c->phys = in.phys;
   c->chain = in.chain;
-  c->force = in.force;
   if (c->N > 0 &&
       cudaHostAlloc((void **)&c->pinned, bead_span(c) + sizeof(DevStatus), cudaHostAllocDefault) !=
           cudaSuccess) {

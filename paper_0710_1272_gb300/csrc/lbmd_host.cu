@@ -80,11 +80,11 @@ Layout make_layout(const lbmd_params &p, bool with_stage) {
   L.lam = take(Np * sizeof(float));
   L.status = take(sizeof(DevStatus));
   L.diag = take((size_t)std::max(p.diag_capacity, 0) * sizeof(DevDiag));
-  // single box with 16-bit populations and a coupled chain: the per-node force
-  // slots of the two-phase spread (16 bytes per node)
-  L.force = with_stage && p.storage != LBMD_STORE_F32 && p.n_beads > 0 && !p.solvent_free
-                ? take((size_t)V * sizeof(float4))
-                : 0;
+  // a chain coupled to the solvent: the spread owner of every node (4 bytes
+  // per node) and the fixed-point impulse sums of the 8 N transfer entries
+  const bool coupled = p.n_beads > 0 && !p.solvent_free;
+  L.owner = coupled ? take((size_t)V * sizeof(int)) : 0;
+  L.acc = coupled ? take(8 * Np * sizeof(SpreadAcc)) : 0;
   L.stage = with_stage ? take(L.stage_floats * sizeof(float)) : 0;
   L.total = o;
   return L;
@@ -356,14 +356,15 @@ cudaError_t init_instance(const lbmd_params &p, const Layout &L, char *ws, cudaS
   DevStatus st{};
   st.t_transloc = -1;
   UP(cudaMemcpyAsync(out.status, &st, sizeof(st), cudaMemcpyHostToDevice, s), "upload");
-  out.force = nullptr;
-  if (L.force) {
-    // force slots at rest: {0, 0, 0, kOwnerFree}, every owner byte 0x7f
-    out.force = (float4 *)(ws + L.force);
-    UP(cudaMemsetAsync(out.force, 0, (size_t)g.V * sizeof(float4), s), "memset");
-    UP(cudaMemset2DAsync((char *)out.force + 12, sizeof(float4), 0x7f, 4, (size_t)g.V, s), "memset");
-  }
   ChainArgs &a = out.chain;
+  a = ChainArgs{};
+  if (L.owner) {
+    // spread owners at rest (every byte 0x7f = kOwnerFree), impulse sums zero
+    a.owner = (int *)(ws + L.owner);
+    a.acc = (SpreadAcc *)(ws + L.acc);
+    UP(cudaMemsetAsync(a.owner, 0x7f, (size_t)g.V * sizeof(int), s), "memset");
+    UP(cudaMemsetAsync(a.acc, 0, 8 * (size_t)std::max(p.n_beads, 1) * sizeof(SpreadAcc), s), "memset");
+  }
   a.geo = g;
   a.has_wall = p.wall_x >= 0;
   a.wall_x = p.wall_x;

@@ -24,7 +24,7 @@ inline size_t store_bytes(int storage) { return storage == LBMD_STORE_F32 ? 4 : 
 // Byte offsets of every buffer of one box inside its workspace slice.
 struct Layout {
   size_t popA, popB, solid, tile, lmask, pos, pos_lo, vel, ui, J, sp_node, sp_w, b0, nl_cnt, wl_cnt,
-      nl_list, wl_list, nl_ref, lam, status, diag, force, stage;
+      nl_list, wl_list, nl_ref, lam, status, diag, owner, acc, stage;
   size_t stage_floats;  // staging capacity in floats (0 without a staging buffer)
   size_t total;
   long long Vp;
@@ -53,7 +53,6 @@ struct Instance {
   ChainArgs chain;
   char *pop[2];
   DevStatus *status;
-  float4 *force;  // two-phase spread slots (16-bit storage), or null
   int has_bonds;
 };
 

@@ -80,6 +80,16 @@ struct LbPhys {
   const long long *step;     // LB steps completed (the noise counter); null: no noise
 };
 
+// Impulse sum of one transfer node in the bead spread (stage 3): the three
+// components as 64-bit fixed point (units of 2^-40) and a flag that is set
+// when a contribution was not finite.  Integer addition is associative, so the
+// sum -- and the populations it is added to -- do not depend on the order in
+// which the (bead, corner) contributions arrive.  At rest all zero.
+struct __align__(32) SpreadAcc {
+  long long x, y, z;
+  long long bad;
+};
+
 // Everything the MD kernel needs for one chain.
 struct ChainArgs {
   LbGeom geo;
@@ -97,6 +107,10 @@ struct ChainArgs {
   float4 *ui, *J;           // interpolated u and impulse of the last step
   int *sp_node;             // [8N] grid node of each transfer weight, -1 none
   float *sp_w;              // [8N] renormalised transfer weights
+  int *owner;               // [V] per node: smallest transfer entry of this step
+                            // that hits it (kOwnerFree at rest)
+  SpreadAcc *acc;           // [8N] impulse sums, at the owner entry of each node
+  int md_accum;             // 1: the MD block adds the impulses to acc itself
   const double *b0;         // [N-1] bond lengths
   int *nl_cnt, *wl_cnt;     // [N] list lengths
   short *nl_list;           // [N][kMaxPairs] partner beads
@@ -183,21 +197,23 @@ cudaError_t launch_read_pulled(int storage, const LbGeom &g, float rho0, const v
                                long long fstride, cudaStream_t s);
 cudaError_t launch_gather(int storage, const ChainArgs &a, cudaStream_t s);
 cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s);
-// Two-phase spread of 16-bit storage through the per-node slots `force`
-// ({Fx, Fy, Fz, owner}, resting at {0, 0, 0, kOwnerFree}; every byte of the
-// owner 0x7f, so a strided memset prepares the field): accumulate (any
-// time after the MD cycle), then apply to `dst` in layout `mode` (after the
-// stream-collide).
+// Spread of the bead impulses (stage 3) in three parts, each independent of
+// the order of concurrent atomics, so that a step gives the same bits in
+// every run:
+//  - the gather claims each transfer node for the smallest (bead, corner)
+//    entry that hits it: atomicMin on owner[node], which rests at kOwnerFree
+//    (every byte 0x7f, so a memset prepares the field);
+//  - accumulate (any time after the MD cycle): every entry adds its share
+//    -w J_i of the impulse to acc[owner] in 64-bit fixed point;
+//  - apply (after the stream-collide): the owner of each node converts the
+//    sum once, adds the source S_p = 3 w_p c_p . F to the node's
+//    post-collision populations of `dst` in layout `mode` (the only write to
+//    those words), and returns owner[node] and acc[owner] to rest.
 constexpr int kOwnerFree = 0x7f7f7f7f;
-cudaError_t launch_spread_accum(const int *sp_node, const float *sp_w, const float4 *J, int nw,
-                                float4 *force, cudaStream_t s);
-cudaError_t launch_spread_apply(int storage, const LbGeom &g, const int *sp_node, int nw,
-                                float4 *force, void *dst, int mode, DevStatus *bump,
-                                cudaStream_t s);
-// Spread into the post-collision populations of `dst`, held in layout `mode`.
-cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, const float *sp_w,
-                          const float4 *J, int N, int nw, void *dst, int mode, DevStatus *bump,
-                          cudaStream_t s);
+cudaError_t launch_spread_accum(const ChainArgs &a, cudaStream_t s);
+// `bump` (may be null): status->step += 1 by one thread.
+cudaError_t launch_spread_apply(int storage, const LbGeom &g, const ChainArgs &a, void *dst,
+                                int mode, DevStatus *bump, cudaStream_t s);
 // Ensemble launchers.  `live` points at the flags of the current step (one int
 // per realisation); realisations whose flag is 0 are skipped by every kernel.
 // Stream-collide: persistent grid of `grid` blocks of 32 x rows threads (rows
@@ -221,9 +237,10 @@ cudaError_t launch_ens_gather(int storage, const EnsMember *mem, const int2 *bea
 // threads each, with dynamic shared memory for `max_n` beads.
 cudaError_t launch_ens_md_cycle(const EnsMember *mem, const int *chains, int count, int threads,
                                 int max_n, const int *live, int priority, cudaStream_t s);
-// Spread of the bead impulses into pop[1 - cur]; bumps each live realisation's
-// step count and writes its flag for the next step into `live_next`
-// (still running and step < *max_steps).
+// Apply part of the spread (the MD blocks of an ensemble accumulate the
+// impulses themselves) into pop[1 - cur]; bumps each live realisation's step
+// count and writes its flag for the next step into `live_next` (still running
+// and step < *max_steps).
 cudaError_t launch_ens_spread(int storage, const EnsMember *mem, const int2 *beads, int nb,
                               const int *live, int *live_next, int cur,
                               const long long *max_steps, cudaStream_t s);

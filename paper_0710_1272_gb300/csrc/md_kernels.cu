@@ -15,9 +15,12 @@
 //     RATTLE: one tridiagonal solve removes the bond-parallel relative
 //             velocities,
 //     J_i += dt (F_drag + F_r);
-//   then the translocation bookkeeping.  k_spread hands -J_i to the fluid with
-//   the gather weights (warp-aggregated atomics into the post-collision
-//   populations, Eq. 10 with the reaction sign).
+//   then the translocation bookkeeping.  The spread hands -J_i to the fluid
+//   with the gather weights (Eq. 10 with the reaction sign): the gather claims
+//   each transfer node for its smallest (bead, corner) entry, the impulses are
+//   summed at that owner in 64-bit fixed point, and the owner adds the source
+//   to the node's post-collision populations once -- so a step gives the same
+//   bits whatever order the atomics take.
 #include "lb_pull.cuh"
 
 namespace lbmd {
@@ -511,6 +514,43 @@ __device__ F3 wall_stencil_forces(const ChainArgs &a, float4 rh, float4 rl) {
   return F;
 }
 
+// Fixed point of the spread: units of 2^-40.  The impulses of a node (|F| of
+// order 1e-2) keep ~30 significant bits, far below a float ulp of the
+// populations they reach; the range (2^23) is far above any finite step.
+constexpr float kFixOne = 1099511627776.0f;  // 2^40
+
+// Adds entry e's share -w_e J_i of the impulse to the sum at the owner of its
+// node (64-bit integer atomics: the result does not depend on their order).
+__device__ __forceinline__ void spread_add(const ChainArgs &a, int e, float4 j) {
+  const int node = a.sp_node[e];
+  if (node < 0) return;
+  const float w = a.sp_w[e];
+  const float fx = -w * j.x, fy = -w * j.y, fz = -w * j.z;
+  SpreadAcc *q = a.acc + a.owner[node];
+  if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) {
+    atomicOr(reinterpret_cast<unsigned long long *>(&q->bad), 1ull);
+    return;
+  }
+  atomicAdd(reinterpret_cast<unsigned long long *>(&q->x), (unsigned long long)__float2ll_rn(fx * kFixOne));
+  atomicAdd(reinterpret_cast<unsigned long long *>(&q->y), (unsigned long long)__float2ll_rn(fy * kFixOne));
+  atomicAdd(reinterpret_cast<unsigned long long *>(&q->z), (unsigned long long)__float2ll_rn(fz * kFixOne));
+}
+
+// The owner's part of the apply: the summed force of node `node`, NaN if a
+// contribution was not finite; the slot and the node's owner return to rest.
+__device__ __forceinline__ F3 spread_take(const ChainArgs &a, int node, int e) {
+  SpreadAcc *q = a.acc + e;
+  const SpreadAcc v = *q;
+  *q = SpreadAcc{0, 0, 0, 0};
+  a.owner[node] = kOwnerFree;
+  if (v.bad) {
+    const float nan = __int_as_float(0x7fc00000);
+    return F3{nan, nan, nan};
+  }
+  const float s = 1.0f / kFixOne;
+  return F3{__ll2float_rn(v.x) * s, __ll2float_rn(v.y) * s, __ll2float_rn(v.z) * s};
+}
+
 // (2) the M MD substeps of one chain, one thread per bead, and (5) the
 // bookkeeping; `a` may live in parameter or shared memory.
 template <bool WS>
@@ -712,6 +752,9 @@ __device__ __forceinline__ void md_cycle_body(const ChainArgs &a) {
     a.vel[i] = f4(v);
     a.J[i] = f4(J);
     a.lam[i] = s_lam[i];
+    if (a.md_accum)  // accumulate part of the spread (3) for the bead's 8 corners
+#pragma unroll
+      for (int k = 0; k < 8; ++k) spread_add(a, 8 * i + k, f4(J));
   }
   // Translocation bookkeeping (Sec. III): unwrapped x = origin + hi + lo
   const float xrel = bead ? ((float)(a.ox - a.wall_x) + rh.x) + rl.x : 0.f;
@@ -853,6 +896,7 @@ __device__ F3 gather_pair(const ChainArgs &a, const void *f, int e, bool valid) 
     a.sp_node[e] = node;
     a.sp_w[e] = wn;
     if (node >= 0) {
+      atomicMin(a.owner + node, e);  // the node's spread owner: its smallest entry
       const int x = node % g.nx, yz = node / g.nx;
       const int y = yz % g.ny, z = yz / g.ny;
       float h[kQ];
@@ -944,125 +988,31 @@ cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, k_md_cycle<1024>, a);
 }
 
-// Sum of F over the lanes in `peers` (the lanes of the warp that hit the same
-// node), added in ascending lane order; lanes that do not `take` part get 0.
-// The loop runs as many rounds as the largest group of the warp has lanes.
-__device__ __forceinline__ F3 peer_sum(unsigned peers, bool take, F3 F) {
-  unsigned rest = take ? peers : 0u;
-  const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(rest));
-  F3 sum{0.f, 0.f, 0.f};
-  for (int r = 0; r < rounds; ++r) {
-    const int src = rest ? __ffs(rest) - 1 : 0;
-    const float vx = __shfl_sync(0xffffffffu, F.x, src);
-    const float vy = __shfl_sync(0xffffffffu, F.y, src);
-    const float vz = __shfl_sync(0xffffffffu, F.z, src);
-    if (rest) {
-      sum = sum + F3{vx, vy, vz};
-      rest &= rest - 1;
-    }
-  }
-  return sum;
-}
-
-// ---------------------------------------------------------------------------
-// (3) extrapolation of the forces: node x_k receives -w_ik J_i as the source
-// S_p = 3 w_p c_p . F (Eq. 10, reaction sign) added to the post-collision
-// populations h*_p(x_k), wherever layout `mode` holds them: [p][x_k] (pull),
-// [opp(p)][x_k] (in place, after an even step), or [p][x_k + c_p] --
-// [opp(p)][x_k] if x_k + c_p is solid -- (in place, after an odd step).
-// Lanes of a warp that hit the same node sum their vectors first (in lane
-// order), and one lane issues the 18 atomic adds.
-// ---------------------------------------------------------------------------
-template <int S>
-__global__ void k_spread(LbGeom g, const int *__restrict__ sp_node, const float *__restrict__ sp_w,
-                         const float4 *__restrict__ J, int nw, typename Store<S>::T *dst, int mode,
-                         DevStatus *bump) {
+// Accumulate part of the spread: one thread per (bead, corner) entry.
+__global__ void __launch_bounds__(256) k_spread_accum(ChainArgs a) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (bump != nullptr && e == 0) bump->step += 1;
-  if (blockIdx.x * blockDim.x >= nw) return;  // whole warp out of range
-  const int lane = threadIdx.x & 31;
-  int node = -1;
-  F3 F{0.f, 0.f, 0.f};
-  if (e < nw) {
-    node = sp_node[e];
-    if (node >= 0) {
-      const float w = sp_w[e];
-      const float4 j = J[e >> 3];
-      F = F3{-w * j.x, -w * j.y, -w * j.z};
-    }
-  }
-  const unsigned peers = __match_any_sync(0xffffffffu, node);
-  const F3 sum = peer_sum(peers, node >= 0, F);
-  const int leader = __ffs(peers) - 1;
-  if (node >= 0 && lane == leader) {
-    using St = Store<S>;
-    const size_t Vp = (size_t)g.Vp;
-    if (mode == kPopAALocal) {
-      const int x = node % g.nx, yz = node / g.nx;
-      const int y = yz % g.ny, z = yz / g.ny;
-      const uint32_t bb = __ldg(&g.lmask[node]);  // bit opp(p): x_k + c_p is solid
-#pragma unroll
-      for (int p = 1; p < kQ; ++p) {
-        const float cf = cx(p) * sum.x + cy(p) * sum.y + cz(p) * sum.z;
-        const size_t t = ((size_t)wrapi(z + cz(p), g.nz) * g.ny + wrapi(y + cy(p), g.ny)) * g.nx +
-                         wrapi(x + cx(p), g.nx);
-        const size_t slot = ((bb >> opp(p)) & 1u) ? (size_t)opp(p) * Vp + node : (size_t)p * Vp + t;
-        St::add(dst + slot, 3.0f * wq(p) * cf);
-      }
-    } else {
-#pragma unroll
-      for (int p = 1; p < kQ; ++p) {
-        const float cf = cx(p) * sum.x + cy(p) * sum.y + cz(p) * sum.z;
-        const int q = mode == kPopAASwap ? opp(p) : p;
-        St::add(dst + (size_t)q * Vp + node, 3.0f * wq(p) * cf);
-      }
-    }
-  }
+  if (e >= 8 * a.N) return;
+  spread_add(a, e, a.J[e >> 3]);
 }
 
-// Two-phase spread for 16-bit population storage.  A 16-bit atomic add per
-// population and corner is slow (neighbouring lanes hit the same words) and
-// rounds each increment to 16 bits before the add.  Instead:
-//  (a) k_spread_accum, right after the MD cycle (beside the stream-collide):
-//      every (bead, corner) adds its force -w_ik J_i to the node's float slot
-//      {Fx, Fy, Fz, owner} and claims the node with the smallest lane index
-//      (atomicMin on owner, which rests at kOwnerFree);
-//  (b) k_spread_apply, after the stream-collide: the owner of each node reads
-//      the summed force, resets the slot, and adds S_p = 3 w_p c_p . F to the
-//      node's post-collision populations (wherever layout `mode` keeps them)
-//      with one plain read-modify-write each: h* <- round16(h* + S_p).
-// Slots are left as they were found, so the field needs clearing only once.
-__global__ void __launch_bounds__(256) k_spread_accum(const int *__restrict__ sp_node,
-                                                      const float *__restrict__ sp_w,
-                                                      const float4 *__restrict__ J, int nw,
-                                                      float4 *force) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nw) return;
-  const int node = sp_node[e];
-  if (node < 0) return;
-  const float w = sp_w[e];
-  const float4 j = J[e >> 3];
-  float *f = reinterpret_cast<float *>(force + node);
-  atomicAdd(f + 0, -w * j.x);
-  atomicAdd(f + 1, -w * j.y);
-  atomicAdd(f + 2, -w * j.z);
-  atomicMin(reinterpret_cast<int *>(f + 3), e);
-}
-
+// (3) extrapolation of the forces: node x_k receives -sum_i w_ik J_i as the
+// source S_p = 3 w_p c_p . F (Eq. 10, reaction sign), added by the node's
+// owner entry to the post-collision populations h*_p(x_k), wherever layout
+// `mode` holds them: [p][x_k] (pull), [opp(p)][x_k] (in place, after an even
+// step), or [p][x_k + c_p] -- [opp(p)][x_k] if x_k + c_p is solid -- (in
+// place, after an odd step).  No other thread writes those words in this
+// kernel: FP32 adds with one atomic each (no read-back); 16-bit storage reads
+// the 18 words first and writes each rounded once.
 template <int S>
 __global__ void __launch_bounds__(256)
-    k_spread_apply(LbGeom g, const int *__restrict__ sp_node, int nw, float4 *force,
-                   typename Store<S>::T *dst, int mode, DevStatus *bump) {
+    k_spread_apply(LbGeom g, ChainArgs a, typename Store<S>::T *dst, int mode, DevStatus *bump) {
   using St = Store<S>;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (bump != nullptr && e == 0) bump->step += 1;
-  if (e >= nw) return;
-  const int node = sp_node[e];
-  if (node < 0) return;
-  float4 *slot = force + node;
-  if (reinterpret_cast<const int *>(slot)[3] != e) return;  // not the owner
-  const float4 F = *slot;
-  *slot = make_float4(0.f, 0.f, 0.f, __int_as_float(kOwnerFree));
+  if (e >= 8 * a.N) return;
+  const int node = a.sp_node[e];
+  if (node < 0 || a.owner[node] != e) return;  // not the owner
+  const F3 F = spread_take(a, node, e);
   const size_t Vp = (size_t)g.Vp;
   uint32_t bb = 0u;
   int x = 0, y = 0, z = 0;
@@ -1073,10 +1023,7 @@ __global__ void __launch_bounds__(256)
     z = yz / g.ny;
     bb = __ldg(&g.lmask[node]);  // bit opp(p): x_k + c_p is solid
   }
-  // all 18 loads first, then the stores: the slots are distinct, and issuing
-  // the loads together takes one memory latency instead of eighteen
   size_t at[kQ];
-  float hv[kQ];
 #pragma unroll
   for (int p = 1; p < kQ; ++p) {
     if (mode == kPopAALocal) {
@@ -1086,54 +1033,40 @@ __global__ void __launch_bounds__(256)
     } else {
       at[p] = (size_t)(mode == kPopAASwap ? opp(p) : p) * Vp + node;
     }
-    hv[p] = St::load_plain(dst + at[p]);
   }
+  if (S == LBMD_STORE_F32) {
 #pragma unroll
-  for (int p = 1; p < kQ; ++p) {
-    const float cf = cx(p) * F.x + cy(p) * F.y + cz(p) * F.z;
-    St::store(dst + at[p], hv[p] + 3.0f * wq(p) * cf);
+    for (int p = 1; p < kQ; ++p)
+      St::add(dst + at[p], 3.0f * wq(p) * (cx(p) * F.x + cy(p) * F.y + cz(p) * F.z));
+  } else {
+    // all 18 loads first, then the stores: one memory latency, not eighteen
+    float hv[kQ];
+#pragma unroll
+    for (int p = 1; p < kQ; ++p) hv[p] = St::load_plain(dst + at[p]);
+#pragma unroll
+    for (int p = 1; p < kQ; ++p)
+      St::store(dst + at[p], hv[p] + 3.0f * wq(p) * (cx(p) * F.x + cy(p) * F.y + cz(p) * F.z));
   }
 }
 
-cudaError_t launch_spread_accum(const int *sp_node, const float *sp_w, const float4 *J, int nw,
-                                float4 *force, cudaStream_t s) {
-  if (nw <= 0) return cudaSuccess;
-  k_spread_accum<<<(nw + 255) / 256, 256, 0, s>>>(sp_node, sp_w, J, nw, force);
+cudaError_t launch_spread_accum(const ChainArgs &a, cudaStream_t s) {
+  if (a.N <= 0) return cudaSuccess;
+  k_spread_accum<<<(8 * a.N + 255) / 256, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_spread_apply(int storage, const LbGeom &g, const int *sp_node, int nw,
-                                float4 *force, void *dst, int mode, DevStatus *bump,
-                                cudaStream_t s) {
-  const int blocks = nw > 0 ? (nw + 255) / 256 : 1;
-  switch (storage) {
-    case LBMD_STORE_F16:
-      k_spread_apply<LBMD_STORE_F16><<<blocks, 256, 0, s>>>(g, sp_node, nw, force, (__half *)dst, mode, bump);
-      break;
-    case LBMD_STORE_BF16:
-      k_spread_apply<LBMD_STORE_BF16><<<blocks, 256, 0, s>>>(g, sp_node, nw, force, (__nv_bfloat16 *)dst, mode, bump);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, const float *sp_w,
-                          const float4 *J, int N, int nw, void *dst, int mode, DevStatus *bump,
-                          cudaStream_t s) {
-  (void)N;
-  const int threads = 256;
-  const int blocks = nw > 0 ? (nw + threads - 1) / threads : 1;
+cudaError_t launch_spread_apply(int storage, const LbGeom &g, const ChainArgs &a, void *dst,
+                                int mode, DevStatus *bump, cudaStream_t s) {
+  const int blocks = a.N > 0 ? (8 * a.N + 255) / 256 : 1;
   switch (storage) {
     case LBMD_STORE_F32:
-      k_spread<LBMD_STORE_F32><<<blocks, threads, 0, s>>>(g, sp_node, sp_w, J, nw, (float *)dst, mode, bump);
+      k_spread_apply<LBMD_STORE_F32><<<blocks, 256, 0, s>>>(g, a, (float *)dst, mode, bump);
       break;
     case LBMD_STORE_F16:
-      k_spread<LBMD_STORE_F16><<<blocks, threads, 0, s>>>(g, sp_node, sp_w, J, nw, (__half *)dst, mode, bump);
+      k_spread_apply<LBMD_STORE_F16><<<blocks, 256, 0, s>>>(g, a, (__half *)dst, mode, bump);
       break;
     case LBMD_STORE_BF16:
-      k_spread<LBMD_STORE_BF16><<<blocks, threads, 0, s>>>(g, sp_node, sp_w, J, nw, (__nv_bfloat16 *)dst, mode, bump);
+      k_spread_apply<LBMD_STORE_BF16><<<blocks, 256, 0, s>>>(g, a, (__nv_bfloat16 *)dst, mode, bump);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -1141,10 +1074,9 @@ cudaError_t launch_spread(int storage, const LbGeom &g, const int *sp_node, cons
   return cudaGetLastError();
 }
 
-// Ensemble spread: same lane layout as k_ens_gather, so a warp holds lanes of
-// one realisation only and matching on the node index suffices.  The first
-// lane of every realisation bumps its step count (if live) and decides
-// whether it takes part in the next step.
+// Ensemble apply: same lane layout as k_ens_gather (the MD blocks have
+// accumulated the impulses).  The first lane of every realisation bumps its
+// step count (if live) and decides whether it takes part in the next step.
 template <int S>
 __global__ void __launch_bounds__(256)
     k_ens_spread(const EnsMember *__restrict__ mem, const int2 *__restrict__ beads, int nb,
@@ -1153,33 +1085,30 @@ __global__ void __launch_bounds__(256)
   using St = Store<S>;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int slot = e >> 3, k = e & 7;
-  const int lane = threadIdx.x & 31;
   int2 mi = make_int2(-1, 0);
   if (slot < nb) mi = beads[slot];
   const bool valid = mi.x >= 0 && live[mi.x];
-  int node = -1;
-  F3 F{0.f, 0.f, 0.f};
   if (valid) {
     const ChainArgs &a = mem[mi.x].a;
     const int ee = 8 * mi.y + k;
-    node = a.sp_node[ee];
-    if (node >= 0) {
-      const float w = a.sp_w[ee];
-      const float4 j = a.J[mi.y];
-      F = F3{-w * j.x, -w * j.y, -w * j.z};
-    }
-  }
-  const unsigned peers = __match_any_sync(0xffffffffu, node);
-  const F3 sum = peer_sum(peers, node >= 0, F);
-  const int leader = __ffs(peers) - 1;
-  if (node >= 0 && lane == leader) {
-    const EnsMember &M = mem[mi.x];
-    typename St::T *dst = (typename St::T *)M.pop[cur ^ 1];
-    const size_t Vp = (size_t)M.a.geo.Vp;
+    const int node = a.sp_node[ee];
+    if (node >= 0 && a.owner[node] == ee) {
+      const F3 F = spread_take(a, node, ee);
+      typename St::T *dst = (typename St::T *)mem[mi.x].pop[cur ^ 1];
+      const size_t Vp = (size_t)a.geo.Vp;
+      if (S == LBMD_STORE_F32) {
 #pragma unroll
-    for (int p = 1; p < kQ; ++p) {
-      const float cf = cx(p) * sum.x + cy(p) * sum.y + cz(p) * sum.z;
-      St::add(dst + (size_t)p * Vp + node, 3.0f * wq(p) * cf);
+        for (int p = 1; p < kQ; ++p)
+          St::add(dst + (size_t)p * Vp + node, 3.0f * wq(p) * (cx(p) * F.x + cy(p) * F.y + cz(p) * F.z));
+      } else {
+        float hv[kQ];
+#pragma unroll
+        for (int p = 1; p < kQ; ++p) hv[p] = St::load_plain(dst + (size_t)p * Vp + node);
+#pragma unroll
+        for (int p = 1; p < kQ; ++p)
+          St::store(dst + (size_t)p * Vp + node,
+                    hv[p] + 3.0f * wq(p) * (cx(p) * F.x + cy(p) * F.y + cz(p) * F.z));
+      }
     }
   }
   if (mi.x >= 0 && mi.y == 0 && k == 0) {

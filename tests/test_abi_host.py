@@ -45,10 +45,10 @@ def test_workspace_covers_two_population_buffers():
         pos = np.zeros((400, 3)) + 130.0
         n = _ws(p, init_pos=pos)
         V = 256 * 128 * 128
-        # two population buffers and the 4-byte link mask of every node (16-bit
-        # storage with a chain: also the 16-byte force slot of the two-phase
-        # spread), plus at most 80 MiB of geometry, bead buffers and staging
-        base = 2 * 19 * V * es + 4 * V + (16 * V if es == 2 else 0)
+        # two population buffers, the 4-byte link mask and the 4-byte spread
+        # owner of every node, plus at most 80 MiB of geometry, bead buffers,
+        # impulse sums and staging
+        base = 2 * 19 * V * es + 4 * V + 4 * V
         assert base <= n <= base + 80 * 2 ** 20
 
 

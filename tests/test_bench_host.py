@@ -17,9 +17,10 @@ class _Args:
 
 def test_launches_per_step():
     p = bench.workload(0, "f32", _Args())
-    assert bench.launches_per_step(p) == 4  # gather, MD cycle, stream-collide, spread
+    # gather, MD cycle, stream-collide, spread accumulate and apply
+    assert bench.launches_per_step(p) == 5
     p = bench.workload(0, "f16", _Args())
-    assert bench.launches_per_step(p) == 5  # the 16-bit spread has two kernels
+    assert bench.launches_per_step(p) == 5
     a = _Args()
     a.workload = "solvent"
     assert bench.launches_per_step(bench.workload(0, "f32", a)) == 1

@@ -98,36 +98,27 @@ def test_ensemble_bead_trajectories_100_steps():
         assert res["t_transloc"][k] == st["t_transloc"], k
 
 
-def test_ensemble_matches_single_box_path():
-    """Ensemble realisations against lbmd_step on the same parameters: same
-    kernels, same lane layout, so they agree to float atomics ordering."""
+def same_state(ens, k, sim):
+    """Ensemble member k and a single-box context hold the same bits."""
+    assert np.array_equal(ens.populations(k), sim.populations()), k
+    rg, vg = ens.beads(k)
+    rs, vs = sim.beads()
+    assert np.array_equal(rg, rs) and np.array_equal(vg, vs), k
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_ensemble_matches_single_box_path(storage):
+    """Ensemble realisations against lbmd_step on the same parameters: the same
+    collision, MD body and fixed-point spread, so the same bits in every
+    storage type."""
     lb = _lb()
-    members, starts = ragged_members()
+    members, starts = ragged_members(storage)
     ens = lb.Ensemble(members, starts)
     ens.step(25)
     for k, (p, pos) in enumerate(zip(members, starts)):
         sim = lb.Simulation(p, init_pos=pos)
         advance_like_member(sim, 25, lb.RUNNING)
-        assert rel_err(ens.populations(k), sim.populations().astype(np.float64)) < 1e-6, k
-        assert np.abs(ens.beads(k)[0] - sim.beads()[0]).max() < 1e-6, k
-
-
-@pytest.mark.parametrize("storage,tol", [("f16", 2e-4), ("bf16", 2e-3)])
-def test_ensemble_half_storage_matches_single_box(storage, tol):
-    """16-bit storage: the bead sources are added by atomics whose order varies
-    from run to run, and every add rounds to the storage type, so two runs may
-    differ by a storage ulp of the deviation |h| <= 0.005 at the touched nodes:
-    relative to the smallest population 1/36 that is 2^-11 * 0.005 * 36 = 9e-5
-    (fp16) and 2^-8 * 0.005 * 36 = 7e-4 (bf16); the bound is twice that."""
-    lb = _lb()
-    members, starts = ragged_members(storage)
-    ens = lb.Ensemble(members, starts)
-    ens.step(10)
-    for k, (p, pos) in enumerate(zip(members, starts)):
-        sim = lb.Simulation(p, init_pos=pos)
-        advance_like_member(sim, 10, lb.RUNNING)
-        assert rel_err(ens.populations(k), sim.populations().astype(np.float64)) < tol, k
-        assert np.abs(ens.beads(k)[0] - sim.beads()[0]).max() < 1e-4, k
+        same_state(ens, k, sim)
 
 
 def test_ensemble_runs_each_member_to_its_translocation():
@@ -177,7 +168,7 @@ def test_ensemble_step_cap_and_resume():
         assert res["steps"][k] == 50
         sim = lb.Simulation(p, init_pos=pos)
         advance_like_member(sim, 50, lb.RUNNING)
-        assert rel_err(ens.populations(k), sim.populations().astype(np.float64)) < 1e-6, k
+        same_state(ens, k, sim)
 
 
 def test_ensemble_autotune_leaves_the_state_unchanged():
@@ -194,8 +185,8 @@ def test_ensemble_autotune_leaves_the_state_unchanged():
     a.step(6)
     b.step(11)
     for k in range(len(members)):
-        assert rel_err(a.populations(k), b.populations(k).astype(np.float64)) < 1e-6, k
-        assert np.abs(a.beads(k)[0] - b.beads(k)[0]).max() < 1e-6, k
+        assert np.array_equal(a.populations(k), b.populations(k)), k
+        assert np.array_equal(a.beads(k)[0], b.beads(k)[0]), k
 
 
 @pytest.mark.parametrize("rows,warps,claim,cpt", [(4, 32, 1, 1), (16, 48, 8, 1), (8, 32, 3, 1),
@@ -211,7 +202,7 @@ def test_ensemble_tile_shapes_agree(rows, warps, claim, cpt):
     a.step(7)
     b.step(7)
     for k in range(len(members)):
-        assert rel_err(a.populations(k), b.populations(k).astype(np.float64)) < 1e-6, k
+        assert np.array_equal(a.populations(k), b.populations(k)), k
 
 
 def test_ensemble_kernel_timing():
@@ -287,7 +278,7 @@ def test_solvent_free_ensemble_matches_oracle():
 
 def test_ensemble_diagnostics_match_single_box():
     """Per-realisation diagnostic records of the ensemble equal those of the
-    single-box path (same kernel body) to float rounding, and stop with the
+    single-box path (same kernel body, same bits), and stop with the
     realisation."""
     lb = _lb()
     members, starts = ragged_members()
@@ -302,9 +293,8 @@ def test_ensemble_diagnostics_match_single_box():
         advance_like_member(sim, 40, lb.RUNNING)
         ds = sim.diagnostics()
         assert list(ds["step"]) == list(d["step"])
-        for key in ("r_u", "r_t", "r_e", "s_h", "s_e", "kinetic"):
-            assert np.allclose(d[key], ds[key], rtol=1e-4, atol=1e-7), (k, key)
-        assert np.array_equal(d["n_trans"], ds["n_trans"])
+        for key in ("r_u", "r_t", "r_e", "s_h", "s_e", "kinetic", "n_trans"):
+            assert np.array_equal(d[key], ds[key]), (k, key)
 
 
 def test_many_small_realisations():
@@ -325,8 +315,7 @@ def test_many_small_realisations():
     for k in (0, 1, 511, 777, 1023):
         sim = lb.Simulation(members[k], init_pos=starts[k])
         advance_like_member(sim, 20, lb.RUNNING)
-        assert rel_err(ens.populations(k), sim.populations().astype(np.float64)) < 1e-6, k
-        assert np.abs(ens.beads(k)[0] - sim.beads()[0]).max() < 1e-6, k
+        same_state(ens, k, sim)
 
 
 def test_ensemble_forcing_and_coupling_variants():

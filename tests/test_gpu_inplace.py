@@ -2,11 +2,11 @@
 FP64 oracle on the same seeded inputs, and against the two-buffer pull path.
 
 The in-place path performs the same arithmetic on the same values as the pull
-path -- only the slots the values are kept in differ -- so without beads the
-two agree bit for bit in every storage type, at every step parity, through
-graph replays of any length and with the thermal source.  With beads the
-spread's atomic additions may round in another order, so the comparison is to
-FP32 rounding.  Against the oracle the bars are those of the pull path:
+path -- only the slots the values are kept in differ -- so the two agree bit
+for bit in every storage type, at every step parity, through graph replays of
+any length, with the thermal source, and with a coupled chain (the spread sums
+each node's impulses in fixed point and adds them once, independent of the
+order of its atomics).  Against the oracle the bars are those of the pull path:
 populations within 1e-5 relative after one step and 1e-4 after 1000, beads
 within 1e-4 over 100 steps.
 """
@@ -191,13 +191,12 @@ def test_inplace_coupled_equals_pull(variant):
     p.update({k: v for k, v in variant.items() if k != "storage"})
     kw = {"storage": variant["storage"]} if "storage" in variant else {}
     a, b = aa_and_pull(p, init_pos=pos, **kw)
-    # FP32: a few ulp of f ~ 0.03; FP16: a few storage ulp of |h| <= 0.005
-    ftol, btol = (2e-5, 1e-4) if kw else (1e-7, 1e-6)
     for n in (1, 1, 16, 3):
         a.step(n)
         b.step(n)
-        assert np.abs(a.populations() - b.populations()).max() <= ftol, n
-        assert np.abs(a.beads()[0] - b.beads()[0]).max() < btol, n
+        assert np.array_equal(a.populations(), b.populations()), n
+        assert np.array_equal(a.beads()[0], b.beads()[0]), n
+        assert np.array_equal(a.beads()[1], b.beads()[1]), n
     assert a.status() == b.status()
 
 
