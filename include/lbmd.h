@@ -53,7 +53,8 @@ extern "C" {
 #define LBMD_RUNNING 0
 #define LBMD_TRANSLOCATED 1 /* every bead on the trans side x < wall_x      */
 #define LBMD_RETRACTED 2    /* crossed, then all beads back past the pore   */
-#define LBMD_NAN 3          /* a bead position or velocity is not finite    */
+#define LBMD_NAN 3          /* a bead position or velocity, or a population
+                               after a stream-collide, is not finite        */
 #define LBMD_SHAKE_FAIL 4   /* the constraint solve did not converge        */
 
 /* ---- option values ----------------------------------------------------- */
@@ -126,7 +127,18 @@ typedef struct lbmd_params {
   const int32_t *bond_i;       /* host, n_constraints entries               */
   const int32_t *bond_j;
   const double *bond_len;
-  const double *init_pos;      /* host, 3*n_beads, unwrapped [i][xyz]        */
+  const double *init_pos;      /* host, 3*n_beads, unwrapped [i][xyz]; NULL:
+                                  the library's seeded start (Sec. III: the
+                                  chain on the cis side, one end in the pore):
+                                  bead 0 at (wall_x + wall_thickness, pore
+                                  centre), bead 1 one bond along +x, then a
+                                  self-avoiding walk of Philox-drawn random
+                                  directions (keyed by seed), every bead
+                                  after the first two at least 2^(1/6) sigma
+                                  from the wall plane, from every solid node
+                                  and from beads two or more places away
+                                  (minimum image).  lbmd_create fails with
+                                  LBMD_EINVAL if no such walk fits the box.  */
   const double *init_vel;      /* host, 3*n_beads or NULL (zero)             */
   const double *init_rho;      /* host, V or NULL (rho0)                     */
   const double *init_u;        /* host, 3*V SoA or NULL                      */
@@ -152,9 +164,12 @@ typedef struct lbmd_diag {
 } lbmd_diag;
 
 /*
- * Bytes of device workspace lbmd_create needs for these parameters (two
- * population buffers -- one with LBMD_STREAM_AA --, the solid bitfield and
- * link masks, bead state and read-out staging).
+ * Bytes of device workspace lbmd_create needs for these parameters: the
+ * state of the Sec. II scheme -- the D3Q19 populations of Eq. 5 (two buffers,
+ * one with LBMD_STREAM_AA), the Sec. III wall as a solid bitfield and link
+ * masks, the bead positions, velocities and neighbour lists of Eqs. 1-4, the
+ * transfer weights and impulse sums of the coupling (Eq. 10) -- and read-out
+ * staging.
  * Validates the parameters; no CUDA call, callable without a GPU.
  * Errors: LBMD_EINVAL (bad parameter, message in lbmd_last_message).
  */
@@ -191,14 +206,17 @@ int lbmd_step(lbmd_ctx *ctx, int64_t n_steps);
 int lbmd_read_fields(lbmd_ctx *ctx, float *rho, float *u, int dst_is_device);
 
 /*
- * The 19 pre-collision populations f_p(x, t) (19*V floats, [19][z][y][x]),
- * i.e. after streaming and bounce-back, before the next collision.  Solid
+ * The 19 pre-collision populations f_p(x, t) of Eq. 5 (19*V floats,
+ * [19][z][y][x]), i.e. after streaming and bounce-back, before the next
+ * collision; the density and velocity of Eqs. 7-8 are their moments.  Solid
  * nodes read 0.  dst_is_device as above.
  */
 int lbmd_read_populations(lbmd_ctx *ctx, float *f, int dst_is_device);
 
 /*
- * Bead positions (unwrapped, 3*n_beads doubles [i][xyz]) and velocities.
+ * Bead positions (unwrapped, 3*n_beads doubles [i][xyz]) and velocities: the
+ * state advanced by the MD substeps of Sec. II (Eqs. 1-4); unwrapped x is what
+ * the Sec. III translocation count N_T compares with wall_x.
  * dst_is_device as above.  Either pointer may be NULL.  A host read-out also
  * fetches the status word in the same synchronisation, so an lbmd_status
  * call before the next lbmd_step does not synchronise again.
@@ -297,9 +315,14 @@ int lbmd_kernel_times(lbmd_ctx *ctx, double *lb_ms, double *md_ms, double *sprea
  * from the previous call, but every call shares it: calls that may overlap on
  * the GPU (unordered streams) race and must be serialised by the caller.  The
  * first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Asynchronous; errors: LBMD_EINVAL (bad parameter, f_in == f_out),
- * LBMD_ESIZE (box beyond the scratch limit), LBMD_ECUDA.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call before any stream capture.  A device reset (cudaDeviceReset)
+ * may move the array: after one, this entry point must not be called again
+ * in the same process.
+ * Asynchronous; errors: LBMD_EINVAL (bad parameter, f_in == f_out,
+ * ny > 524280), LBMD_EUNSUPPORTED (see params), LBMD_ESIZE (box beyond the
+ * scratch limit), LBMD_ECUDA (a launch failed; the status is that of this
+ * call's own launches).
  */
 int lbmd_lb_step_noalloc(const lbmd_params *params, const float *f_in, float *f_out,
                          void *cuda_stream);

@@ -376,6 +376,19 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
   *out = nullptr;
   int rc = validate_members(members, count);
   if (rc) return rc;
+  // members without init_pos start from the library's seeded walk
+  std::vector<lbmd_params> given(members, members + count);
+  std::vector<std::vector<double>> starts(count);
+  for (int m = 0; m < count; ++m)
+    if (!given[m].init_pos) {
+      if ((rc = seeded_start(given[m], starts[m])) != LBMD_OK) {
+        char buf[512];
+        snprintf(buf, sizeof(buf), "%s", last_message());
+        return fail(rc, "member %d: %s", m, buf);
+      }
+      given[m].init_pos = starts[m].data();
+    }
+  members = given.data();
   EnsLayout E = make_ens_layout(members, count);
   if (!dev_workspace || bytes < E.total)
     return fail(LBMD_ESIZE, "workspace of %zu bytes, %zu needed", bytes, E.total);
@@ -453,7 +466,9 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
     EnsMember &M = e->hmem[m];
     memset(&M, 0, sizeof(M));
     M.a = e->inst[m].chain;
-    M.a.md_accum = 1;  // the MD blocks accumulate the spread (beside the stream-collide)
+    // the MD blocks of coupled chains sum the spread (beside the stream-collide);
+    // without a solvent there are no spread buffers (owner, acc, sp_src null)
+    M.a.md_accum = M.a.sp_src != nullptr ? 1 : 0;
     M.a.f = nullptr;
     M.a.f_mode = kPopPull;
     M.ph = e->inst[m].phys;
@@ -476,6 +491,7 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
     D.rho0 = M.ph.rho0;
     for (int a = 0; a < 3; ++a) D.g[a] = M.ph.g[a];
     D.forcing = M.ph.forcing;
+    D.nonfinite = M.ph.nonfinite;
   }
   // (realisation, bead) slots, each realisation padded to a multiple of four
   std::vector<int2> beads;

@@ -86,6 +86,9 @@ __device__ __forceinline__ void collide19(float h[kQ], const LbPhys &ph, uint32_
   float drho, jx, jy, jz;
   moments19(h, drho, jx, jy, jz);
   const float rho = ph.rho0 + drho;
+  // a population that is not finite makes the density not finite: flag it
+  // (one compare and a predicated store per node)
+  if (!isfinite(rho)) *ph.nonfinite = 1;
   const float inv = __frcp_rn(rho);  // correctly rounded, as 1.0f / rho
   float ux, uy, uz;
   if (FORCING == LBMD_FORCING_GUO) {

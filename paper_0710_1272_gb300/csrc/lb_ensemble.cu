@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(32 * ROWS, WARPS / ROWS)
       ph.g[1] = d.g[1];
       ph.g[2] = d.g[2];
       ph.forcing = FORCING;
+      ph.nonfinite = d.nonfinite;
       // node of this thread: row-major index r in the plane, its row by a
       // float reciprocal with a one-step correction (exact for nx * ny < 2^22)
       const int plane = d.nx * d.ny;

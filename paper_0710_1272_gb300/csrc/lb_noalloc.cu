@@ -180,8 +180,8 @@ extern "C" int lbmd_lb_step_noalloc(const lbmd_params *p, const float *f_in, flo
   if (f_in == f_out) return LBMD_EINVAL;
   if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nz > 65535) return LBMD_EINVAL;
   if (!(p->tau > 0.5) || !(p->rho0 > 0)) return LBMD_EINVAL;
-  if (p->storage != LBMD_STORE_F32 || p->n_beads != 0) return LBMD_EINVAL;
-  if (p->kT_fluid != 0.0) return LBMD_EUNSUPPORTED;  // no step counter for the noise
+  // FP32 solvent only: no bead state to keep, no step counter for the noise
+  if (p->storage != LBMD_STORE_F32 || p->n_beads != 0 || p->kT_fluid != 0.0) return LBMD_EUNSUPPORTED;
   if (p->forcing != LBMD_FORCING_PAPER && p->forcing != LBMD_FORCING_GUO) return LBMD_EINVAL;
   if (p->wall_x < -1 || p->wall_x >= p->nx) return LBMD_EINVAL;
   if (p->y_walls != 0 && p->y_walls != 1) return LBMD_EINVAL;
@@ -205,25 +205,32 @@ extern "C" int lbmd_lb_step_noalloc(const lbmd_params *p, const float *f_in, flo
   }
   const long long tiles = (long long)q.ny * q.nz * q.ntx;
   if (tiles > kNoAllocMaxTiles) return LBMD_ESIZE;  // box larger than the fixed scratch
+  if ((q.ny + 7) / 8 > 65535) return LBMD_EINVAL;   // grid y of the step kernel (ny <= 524280)
 
   uint32_t *scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) return LBMD_ECUDA;
   uint32_t *bits = scratch;
   uint8_t *tile = (uint8_t *)(scratch + kNoAllocMaxTiles);
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  const int tb = 256;
-  const unsigned gb = (unsigned)((tiles + tb - 1) / tb);
-  k_noalloc_bits<<<gb, tb, 0, s>>>(q, bits);
-  k_noalloc_tiles<<<gb, tb, 0, s>>>(q, bits, tile);
-  dim3 block(32, 8);
-  dim3 grid(q.ntx, (q.ny + 7) / 8, q.nz);
-  const float omega = (float)(1.0 / p->tau);
+  // launched with cudaLaunchKernelEx, whose return value is the status of
+  // that launch alone (not an error left behind by unrelated earlier work)
+  cudaLaunchConfig_t cfg = {};
+  cfg.stream = (cudaStream_t)cuda_stream;
+  cfg.blockDim = dim3(256);
+  cfg.gridDim = dim3((unsigned)((tiles + 255) / 256));
+  if (cudaLaunchKernelEx(&cfg, k_noalloc_bits, q, bits) != cudaSuccess) return LBMD_ECUDA;
+  if (cudaLaunchKernelEx(&cfg, k_noalloc_tiles, q, (const uint32_t *)bits, tile) != cudaSuccess)
+    return LBMD_ECUDA;
+  cfg.blockDim = dim3(32, 8);
+  cfg.gridDim = dim3(q.ntx, (q.ny + 7) / 8, q.nz);
+  const float omega = (float)(1.0 / p->tau), rho0 = (float)p->rho0;
   const float gx = (float)p->body_force[0], gy = (float)p->body_force[1], gz = (float)p->body_force[2];
-  if (p->forcing == LBMD_FORCING_GUO)
-    k_noalloc_step<LBMD_FORCING_GUO><<<grid, block, 0, s>>>(q, omega, (float)p->rho0, gx, gy, gz, bits,
-                                                           tile, f_in, f_out);
-  else
-    k_noalloc_step<LBMD_FORCING_PAPER><<<grid, block, 0, s>>>(q, omega, (float)p->rho0, gx, gy, gz, bits,
-                                                             tile, f_in, f_out);
-  return cudaGetLastError() == cudaSuccess ? LBMD_OK : LBMD_ECUDA;
+  const uint32_t *cbits = bits;
+  const uint8_t *ctile = tile;
+  const cudaError_t e =
+      p->forcing == LBMD_FORCING_GUO
+          ? cudaLaunchKernelEx(&cfg, k_noalloc_step<LBMD_FORCING_GUO>, q, omega, rho0, gx, gy, gz, cbits,
+                               ctile, f_in, f_out)
+          : cudaLaunchKernelEx(&cfg, k_noalloc_step<LBMD_FORCING_PAPER>, q, omega, rho0, gx, gy, gz, cbits,
+                               ctile, f_in, f_out);
+  return e == cudaSuccess ? LBMD_OK : LBMD_ECUDA;
 }

@@ -119,8 +119,8 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     if ((e = cudaStreamWaitEvent(c->side, c->ev_fork, 0)) != cudaSuccess) return e;
     if ((e = launch_md_cycle(a, c->prio_high, c->side)) != cudaSuccess) return e;
     if (t[3] && (e = cudaEventRecord(t[3], c->side)) != cudaSuccess) return e;
-    // accumulate part of the spread, beside the stream-collide
-    if ((e = launch_spread_accum(c->chain, c->side)) != cudaSuccess) return e;
+    // sum part of the spread, beside the stream-collide
+    if ((e = launch_spread_sum(c->chain, c->side)) != cudaSuccess) return e;
   } else if (t[2]) {
     if ((e = cudaEventRecord(t[2], c->own)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(t[3], c->own)) != cudaSuccess) return e;
@@ -237,7 +237,13 @@ int lbmd_create(const lbmd_params *params, void *dev_workspace, size_t bytes, vo
   *out = nullptr;
   int rc = validate(params);
   if (rc) return rc;
-  const lbmd_params &p = *params;
+  // without init_pos the chain starts from the library's seeded walk
+  lbmd_params p = *params;
+  std::vector<double> start;
+  if (!p.init_pos && p.n_beads > 0) {
+    if ((rc = seeded_start(p, start)) != LBMD_OK) return rc;
+    p.init_pos = start.data();
+  }
   Layout L = make_layout(p, true);
   if (!dev_workspace || bytes < L.total)
     return fail(LBMD_ESIZE, "workspace of %zu bytes, %zu needed", bytes, L.total);
@@ -461,7 +467,8 @@ int lbmd_status(lbmd_ctx *c, int64_t *step, int32_t *n_trans, int32_t *state, in
   }
   if (step) *step = st.step;
   if (n_trans) *n_trans = st.n_trans;
-  if (state) *state = st.state;
+  // a box without beads has no apply kernel to fold the population flag in
+  if (state) *state = st.state == LBMD_RUNNING && st.pop_bad ? LBMD_NAN : st.state;
   if (t_transloc) *t_transloc = st.t_transloc;
   return LBMD_OK;
 }

@@ -3,6 +3,8 @@
 // single-box context and the ensemble.  No device memory is allocated here.
 #include "lbmd_host.h"
 
+#include "lbmd_common.cuh"
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -81,10 +83,12 @@ Layout make_layout(const lbmd_params &p, bool with_stage) {
   L.status = take(sizeof(DevStatus));
   L.diag = take((size_t)std::max(p.diag_capacity, 0) * sizeof(DevDiag));
   // a chain coupled to the solvent: the spread owner of every node (4 bytes
-  // per node) and the fixed-point impulse sums of the 8 N transfer entries
+  // per node), the fixed-point impulse sums and the apply records of the 8 N
+  // transfer entries
   const bool coupled = p.n_beads > 0 && !p.solvent_free;
   L.owner = coupled ? take((size_t)V * sizeof(int)) : 0;
   L.acc = coupled ? take(8 * Np * sizeof(SpreadAcc)) : 0;
+  L.sp_src = coupled ? take(8 * Np * sizeof(float4)) : 0;
   L.stage = with_stage ? take(L.stage_floats * sizeof(float)) : 0;
   L.total = o;
   return L;
@@ -134,7 +138,6 @@ int validate(const lbmd_params *p) {
   if (p->n_beads > 0) {
     if (p->md_substeps < 1 || p->md_substeps > 255)
       return fail(LBMD_EINVAL, "md_substeps must be in [1, 255]");
-    if (!p->init_pos) return fail(LBMD_EINVAL, "init_pos is required when n_beads > 0");
     if (!(p->bead_mass > 0) || !(p->gamma >= 0) || !(p->kT >= 0) || !(p->lj_sigma > 0) ||
         !(p->lj_eps >= 0) || !(p->kappa_phi >= 0) || !std::isfinite(p->f_drive))
       return fail(LBMD_EINVAL, "bead parameters out of range");
@@ -154,8 +157,9 @@ int validate(const lbmd_params *p) {
     }
     if (params_have_bonds(*p) && (p->shake_max_iter < 1 || !(p->shake_tol > 0)))
       return fail(LBMD_EINVAL, "shake_max_iter >= 1 and shake_tol > 0 required");
-    for (int i = 0; i < 3 * p->n_beads; ++i)
-      if (!std::isfinite(p->init_pos[i])) return fail(LBMD_EINVAL, "init_pos not finite");
+    if (p->init_pos)
+      for (int i = 0; i < 3 * p->n_beads; ++i)
+        if (!std::isfinite(p->init_pos[i])) return fail(LBMD_EINVAL, "init_pos not finite");
   }
   return LBMD_OK;
 }
@@ -178,6 +182,96 @@ static bool is_solid(const lbmd_params &p, int x, int y, int z) {
   pore_origin(p, y0, z0);
   const bool in_pore = p.pore_d > 0 && y >= y0 && y < y0 + p.pore_d && z >= z0 && z < z0 + p.pore_d;
   return !in_pore;
+}
+
+// Seeded start (Sec. III; reading of the walk: bead 0 at the pore mouth,
+// x_w + t at the pore centre, bead 1 one bond further along +x, every later
+// bead one bond in a uniformly random direction from the previous one,
+// rejected if it comes within 2^(1/6) sigma of a bead two or more places
+// away along the chain (minimum image), of a solid node, or of the wall plane
+// (x < x_w + t - 1 + 2^(1/6) sigma), or beyond x_w + n_x - 2^(1/6) sigma;
+// after 1000 rejections of one bead the walk restarts).  Random numbers:
+// Philox4x32-10 keyed by the seed, counter (bead, attempt, restart, 1 << 8)
+// -- stream 1, beside the bead noise (stream 0) and the fluid noise
+// (stream 2); direction from two uniforms: cos(theta) = 2 u1 - 1,
+// phi = 2 pi u2.
+int seeded_start(const lbmd_params &p, std::vector<double> &pos) {
+  const int N = p.n_beads;
+  pos.assign(3 * (size_t)std::max(N, 0), 0.0);
+  if (N <= 0) return LBMD_OK;
+  const double rc = 1.122462048309373 * p.lj_sigma, rc2 = rc * rc;
+  const double L[3] = {(double)p.nx, (double)p.ny, (double)p.nz};
+  auto bond = [&](int k) {  // length of the bond (k, k + 1)
+    if (p.n_constraints > 0) return p.bond_len[k];
+    return p.bond_length > 0 ? p.bond_length : rc;
+  };
+  double start[3], x_lo = -INFINITY, x_hi = INFINITY;
+  const int t = p.wall_thickness;
+  if (p.wall_x >= 0) {
+    int y0, z0;
+    pore_origin(p, y0, z0);
+    start[0] = p.wall_x + t;
+    start[1] = y0 + 0.5 * (p.pore_d - 1);
+    start[2] = z0 + 0.5 * (p.pore_d - 1);
+    x_lo = p.wall_x + t - 1 + rc;
+    x_hi = p.wall_x + L[0] - rc;
+  } else {
+    for (int a = 0; a < 3; ++a) start[a] = 0.5 * L[a];
+  }
+  auto min_image = [&](double d, int a) { return d - L[a] * std::floor(d / L[a] + 0.5); };
+  auto near_solid = [&](const double *r) {
+    if (p.wall_x < 0 && !p.y_walls) return false;
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = (int)std::ceil(r[a] - rc);
+      hi[a] = (int)std::floor(r[a] + rc);
+    }
+    for (int x = lo[0]; x <= hi[0]; ++x)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int z = lo[2]; z <= hi[2]; ++z) {
+          const double dx = x - r[0], dy = y - r[1], dz = z - r[2];
+          if (dx * dx + dy * dy + dz * dz >= rc2) continue;
+          const int wx = ((x % p.nx) + p.nx) % p.nx, wy = ((y % p.ny) + p.ny) % p.ny,
+                    wz = ((z % p.nz) + p.nz) % p.nz;
+          if (is_solid(p, wx, wy, wz)) return true;
+        }
+    return false;
+  };
+  const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
+  for (uint32_t restart = 0; restart < 1000; ++restart) {
+    for (int a = 0; a < 3; ++a) pos[a] = start[a];
+    if (N > 1) {
+      pos[3] = start[0] + bond(0);
+      pos[4] = start[1];
+      pos[5] = start[2];
+    }
+    bool ok = true;
+    for (int i = 2; i < N && ok; ++i) {
+      const double b = bond(i - 1);
+      bool placed = false;
+      for (uint32_t attempt = 0; attempt < 1000 && !placed; ++attempt) {
+        const U4 r = philox4x32_10(U4{(uint32_t)i, attempt, restart, 1u << 8}, k0, k1);
+        const double u1 = ((r.x >> 9) + 0.5) * 0x1p-23, u2 = ((r.y >> 9) + 0.5) * 0x1p-23;
+        const double ct = 2.0 * u1 - 1.0, st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+        const double ph = 2.0 * M_PI * u2;
+        double c[3] = {pos[3 * (i - 1)] + b * st * std::cos(ph), pos[3 * (i - 1) + 1] + b * st * std::sin(ph),
+                       pos[3 * (i - 1) + 2] + b * ct};
+        if (!(c[0] >= x_lo && c[0] <= x_hi)) continue;
+        bool clash = false;
+        for (int j = 0; j + 1 < i && !clash; ++j) {
+          const double dx = min_image(c[0] - pos[3 * j], 0), dy = min_image(c[1] - pos[3 * j + 1], 1),
+                       dz = min_image(c[2] - pos[3 * j + 2], 2);
+          clash = dx * dx + dy * dy + dz * dz < rc2;
+        }
+        if (clash || near_solid(c)) continue;
+        for (int a = 0; a < 3; ++a) pos[3 * i + a] = c[a];
+        placed = true;
+      }
+      ok = placed;
+    }
+    if (ok) return LBMD_OK;
+  }
+  return fail(LBMD_EINVAL, "no self-avoiding chain start of %d beads fits the box", N);
 }
 
 namespace {
@@ -295,6 +389,7 @@ cudaError_t init_instance(const lbmd_params &p, const Layout &L, char *ws, cudaS
   out.phys.forcing = p.forcing;
   out.phys.seed = p.seed;
   out.phys.step = nullptr;
+  out.phys.nonfinite = &out.status->pop_bad;
   for (int k = 0; k < 15; ++k) out.phys.fl_amp[k] = 0.f;
   if (p.kT_fluid > 0) {
     fluct_amplitudes(p.kT_fluid, p.tau, out.phys.fl_amp);
@@ -359,11 +454,15 @@ cudaError_t init_instance(const lbmd_params &p, const Layout &L, char *ws, cudaS
   ChainArgs &a = out.chain;
   a = ChainArgs{};
   if (L.owner) {
-    // spread owners at rest (every byte 0x7f = kOwnerFree), impulse sums zero
+    // spread owners at rest (every byte 0x7f = kOwnerFree), impulse sums zero,
+    // apply records without a node (-1)
+    const size_t ne = 8 * (size_t)std::max(p.n_beads, 1);
     a.owner = (int *)(ws + L.owner);
     a.acc = (SpreadAcc *)(ws + L.acc);
+    a.sp_src = (float4 *)(ws + L.sp_src);
     UP(cudaMemsetAsync(a.owner, 0x7f, (size_t)g.V * sizeof(int), s), "memset");
-    UP(cudaMemsetAsync(a.acc, 0, 8 * (size_t)std::max(p.n_beads, 1) * sizeof(SpreadAcc), s), "memset");
+    UP(cudaMemsetAsync(a.acc, 0, ne * sizeof(SpreadAcc), s), "memset");
+    UP(cudaMemsetAsync(a.sp_src, 0xff, ne * sizeof(float4), s), "memset");
   }
   a.geo = g;
   a.has_wall = p.wall_x >= 0;

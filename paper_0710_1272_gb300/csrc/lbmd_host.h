@@ -24,7 +24,7 @@ inline size_t store_bytes(int storage) { return storage == LBMD_STORE_F32 ? 4 : 
 // Byte offsets of every buffer of one box inside its workspace slice.
 struct Layout {
   size_t popA, popB, solid, tile, lmask, pos, pos_lo, vel, ui, J, sp_node, sp_w, b0, nl_cnt, wl_cnt,
-      nl_list, wl_list, nl_ref, lam, status, diag, owner, acc, stage;
+      nl_list, wl_list, nl_ref, lam, status, diag, owner, acc, sp_src, stage;
   size_t stage_floats;  // staging capacity in floats (0 without a staging buffer)
   size_t total;
   long long Vp;
@@ -41,6 +41,12 @@ long long chunk_cells_for(const lbmd_params &p);
 
 int validate(const lbmd_params *p);
 bool params_have_bonds(const lbmd_params &p);
+
+// The library's own initial chain for params with init_pos == NULL (Sec. III:
+// the chain starts on the cis side with one end in the pore): a seeded
+// off-lattice self-avoiding walk, 3 n_beads doubles [i][xyz] (unwrapped).
+// Returns LBMD_OK, or LBMD_EINVAL when no such walk fits the box.
+int seeded_start(const lbmd_params &p, std::vector<double> &pos);
 
 // Copy the diagnostic records of one chain to the host (synchronises s).
 int copy_diagnostics(const DevStatus *status, const DevDiag *diag, int cap, lbmd_diag *records,

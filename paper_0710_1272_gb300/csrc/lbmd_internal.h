@@ -22,6 +22,8 @@ struct DevStatus {
   int nl_ok;             // 1 if the current lists hold every pair (no overflow)
   int out_buf;           // ensemble: population buffer (0/1) written by the last step
   int diag_count;        // diagnostic records written
+  int pop_bad;           // 1 once a stream-collide met a node whose populations
+                         // are not all finite (density not finite)
 };
 
 // One record of the Sec. III chain diagnostics (end of an LB step).
@@ -78,6 +80,7 @@ struct LbPhys {
   float fl_amp[15];          // a_k = sqrt(3 kT (1 - (1 - omega)^2) / b_k), k = 4..18
   unsigned long long seed;   // Philox key
   const long long *step;     // LB steps completed (the noise counter); null: no noise
+  int *nonfinite;            // set to 1 by a collision whose density is not finite
 };
 
 // Impulse sum of one transfer node in the bead spread (stage 3): the three
@@ -110,7 +113,9 @@ struct ChainArgs {
   int *owner;               // [V] per node: smallest transfer entry of this step
                             // that hits it (kOwnerFree at rest)
   SpreadAcc *acc;           // [8N] impulse sums, at the owner entry of each node
-  int md_accum;             // 1: the MD block adds the impulses to acc itself
+  float4 *sp_src;           // [8N] per entry: at a node's owner (F_x, F_y, F_z, node)
+                            // with F the node's summed force; elsewhere node = -1
+  int md_accum;             // 1: the MD block sums the impulses itself
   const double *b0;         // [N-1] bond lengths
   int *nl_cnt, *wl_cnt;     // [N] list lengths
   short *nl_list;           // [N][kMaxPairs] partner beads
@@ -132,7 +137,7 @@ struct EnsMember {
 };
 
 // What the ensemble stream-collide needs of one realisation, 16-byte aligned
-// so that a block reads it with five vector loads.
+// so that a block reads it with six vector loads.
 struct __align__(16) EnsLb {
   void *pop[2];                 // post-collision populations, swapped every step
   const uint32_t *lmask;        // as LbGeom::lmask
@@ -143,6 +148,7 @@ struct __align__(16) EnsLb {
   float omega, rho0;
   float g[3];
   int forcing;
+  int *nonfinite;               // the realisation's DevStatus::pop_bad
 };
 
 // Work item of the ensemble stream-collide: 32 x rows consecutive nodes
@@ -197,20 +203,22 @@ cudaError_t launch_read_pulled(int storage, const LbGeom &g, float rho0, const v
                                long long fstride, cudaStream_t s);
 cudaError_t launch_gather(int storage, const ChainArgs &a, cudaStream_t s);
 cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s);
-// Spread of the bead impulses (stage 3) in three parts, each independent of
-// the order of concurrent atomics, so that a step gives the same bits in
-// every run:
+// Spread of the bead impulses (stage 3), independent of the order of
+// concurrent atomics, so that a step gives the same bits in every run:
 //  - the gather claims each transfer node for the smallest (bead, corner)
 //    entry that hits it: atomicMin on owner[node], which rests at kOwnerFree
 //    (every byte 0x7f, so a memset prepares the field);
-//  - accumulate (any time after the MD cycle): every entry adds its share
-//    -w J_i of the impulse to acc[owner] in 64-bit fixed point;
-//  - apply (after the stream-collide): the owner of each node converts the
-//    sum once, adds the source S_p = 3 w_p c_p . F to the node's
-//    post-collision populations of `dst` in layout `mode` (the only write to
-//    those words), and returns owner[node] and acc[owner] to rest.
+//  - sum (any time after the MD cycle; all contributions to a box come from
+//    its one chain): every entry adds its share -w J_i of the impulse to
+//    acc[owner] in 64-bit fixed point; then each owner converts its sum once
+//    into sp_src[owner] = (F, node), and returns acc and owner[node] to rest;
+//  - apply (after the stream-collide): each owner entry adds the source
+//    S_p = 3 w_p c_p . F to its node's post-collision populations of `dst` in
+//    layout `mode` -- the only write to those words.
+// launch_spread_sum enqueues the sum as two kernels (chains whose MD block
+// sums instead have md_accum set).
 constexpr int kOwnerFree = 0x7f7f7f7f;
-cudaError_t launch_spread_accum(const ChainArgs &a, cudaStream_t s);
+cudaError_t launch_spread_sum(const ChainArgs &a, cudaStream_t s);
 // `bump` (may be null): status->step += 1 by one thread.
 cudaError_t launch_spread_apply(int storage, const LbGeom &g, const ChainArgs &a, void *dst,
                                 int mode, DevStatus *bump, cudaStream_t s);
@@ -237,8 +245,8 @@ cudaError_t launch_ens_gather(int storage, const EnsMember *mem, const int2 *bea
 // threads each, with dynamic shared memory for `max_n` beads.
 cudaError_t launch_ens_md_cycle(const EnsMember *mem, const int *chains, int count, int threads,
                                 int max_n, const int *live, int priority, cudaStream_t s);
-// Apply part of the spread (the MD blocks of an ensemble accumulate the
-// impulses themselves) into pop[1 - cur]; bumps each live realisation's step
+// Apply part of the spread (the MD blocks of an ensemble sum the impulses
+// themselves) into pop[1 - cur]; bumps each live realisation's step
 // count and writes its flag for the next step into `live_next` (still running
 // and step < *max_steps).
 cudaError_t launch_ens_spread(int storage, const EnsMember *mem, const int2 *beads, int nb,

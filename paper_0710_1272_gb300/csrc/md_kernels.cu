@@ -516,18 +516,23 @@ __device__ F3 wall_stencil_forces(const ChainArgs &a, float4 rh, float4 rl) {
 
 // Fixed point of the spread: units of 2^-40.  The impulses of a node (|F| of
 // order 1e-2) keep ~30 significant bits, far below a float ulp of the
-// populations they reach; the range (2^23) is far above any finite step.
+// populations they reach.
 constexpr float kFixOne = 1099511627776.0f;  // 2^40
 
 // Adds entry e's share -w_e J_i of the impulse to the sum at the owner of its
 // node (64-bit integer atomics: the result does not depend on their order).
+// A share that is not finite, or too large for the fixed point (|F| >= 2^10:
+// then even all 8 N <= 2^13 shares of a chain on one node stay below 2^63 in
+// units of 2^-40), marks the sum instead, and the node receives NaN -- a
+// stable step hands the fluid impulses of order 1e-2.
 __device__ __forceinline__ void spread_add(const ChainArgs &a, int e, float4 j) {
   const int node = a.sp_node[e];
   if (node < 0) return;
   const float w = a.sp_w[e];
   const float fx = -w * j.x, fy = -w * j.y, fz = -w * j.z;
   SpreadAcc *q = a.acc + a.owner[node];
-  if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) {
+  const float lim = 1024.0f;  // 2^10
+  if (!(fabsf(fx) < lim && fabsf(fy) < lim && fabsf(fz) < lim)) {
     atomicOr(reinterpret_cast<unsigned long long *>(&q->bad), 1ull);
     return;
   }
@@ -536,19 +541,33 @@ __device__ __forceinline__ void spread_add(const ChainArgs &a, int e, float4 j) 
   atomicAdd(reinterpret_cast<unsigned long long *>(&q->z), (unsigned long long)__float2ll_rn(fz * kFixOne));
 }
 
-// The owner's part of the apply: the summed force of node `node`, NaN if a
-// contribution was not finite; the slot and the node's owner return to rest.
+// The owner's conversion: the summed force of node `node` (NaN if a
+// contribution was not finite); the sum and the node's owner return to rest.
+// The sum is read through L2: within an MD block it was written by other
+// threads' atomics before a barrier.
 __device__ __forceinline__ F3 spread_take(const ChainArgs &a, int node, int e) {
   SpreadAcc *q = a.acc + e;
-  const SpreadAcc v = *q;
+  const long long x = __ldcg(&q->x), y = __ldcg(&q->y), z = __ldcg(&q->z), bad = __ldcg(&q->bad);
   *q = SpreadAcc{0, 0, 0, 0};
   a.owner[node] = kOwnerFree;
-  if (v.bad) {
+  if (bad) {
     const float nan = __int_as_float(0x7fc00000);
     return F3{nan, nan, nan};
   }
   const float s = 1.0f / kFixOne;
-  return F3{__ll2float_rn(v.x) * s, __ll2float_rn(v.y) * s, __ll2float_rn(v.z) * s};
+  return F3{__ll2float_rn(x) * s, __ll2float_rn(y) * s, __ll2float_rn(z) * s};
+}
+
+// After every contribution is summed: entry e's record for the apply --
+// (F, node) if e owns its node, node = -1 otherwise.
+__device__ __forceinline__ void spread_finalize(const ChainArgs &a, int e) {
+  const int node = a.sp_node[e];
+  float4 out = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+  if (node >= 0 && a.owner[node] == e) {
+    const F3 F = spread_take(a, node, e);
+    out = make_float4(F.x, F.y, F.z, __int_as_float(node));
+  }
+  a.sp_src[e] = out;
 }
 
 // (2) the M MD substeps of one chain, one thread per bead, and (5) the
@@ -752,7 +771,7 @@ __device__ __forceinline__ void md_cycle_body(const ChainArgs &a) {
     a.vel[i] = f4(v);
     a.J[i] = f4(J);
     a.lam[i] = s_lam[i];
-    if (a.md_accum)  // accumulate part of the spread (3) for the bead's 8 corners
+    if (a.md_accum)  // spread (3): the bead's 8 corner shares into the sums
 #pragma unroll
       for (int k = 0; k < 8; ++k) spread_add(a, 8 * i + k, f4(J));
   }
@@ -761,6 +780,10 @@ __device__ __forceinline__ void md_cycle_body(const ChainArgs &a) {
   const bool finite = isfinite(rh.x) && isfinite(rh.y) && isfinite(rh.z) && isfinite(v.x) &&
                       isfinite(v.y) && isfinite(v.z);
   const int nt = __syncthreads_count(bead && a.has_wall && xrel < 0.f);
+  // every share of this chain is summed (barrier above): the owners' records
+  if (a.md_accum && bead)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) spread_finalize(a, 8 * i + k);
   const int nan = __syncthreads_or(bead && !finite);
   const int out = __syncthreads_and(!bead || xrel > (float)(a.wall_t - 1) + 1.5f);
   const int bad = __syncthreads_or(shake_bad);
@@ -988,11 +1011,16 @@ cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, k_md_cycle<1024>, a);
 }
 
-// Accumulate part of the spread: one thread per (bead, corner) entry.
+// The sum of the spread as two kernels, one thread per (bead, corner) entry.
 __global__ void __launch_bounds__(256) k_spread_accum(ChainArgs a) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= 8 * a.N) return;
   spread_add(a, e, a.J[e >> 3]);
+}
+__global__ void __launch_bounds__(256) k_spread_finalize(ChainArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 8 * a.N) return;
+  spread_finalize(a, e);
 }
 
 // (3) extrapolation of the forces: node x_k receives -sum_i w_ik J_i as the
@@ -1005,14 +1033,20 @@ __global__ void __launch_bounds__(256) k_spread_accum(ChainArgs a) {
 // the 18 words first and writes each rounded once.
 template <int S>
 __global__ void __launch_bounds__(256)
-    k_spread_apply(LbGeom g, ChainArgs a, typename Store<S>::T *dst, int mode, DevStatus *bump) {
+    k_spread_apply(LbGeom g, const float4 *__restrict__ src, int nw, typename Store<S>::T *dst,
+                   int mode, DevStatus *bump) {
   using St = Store<S>;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (bump != nullptr && e == 0) bump->step += 1;
-  if (e >= 8 * a.N) return;
-  const int node = a.sp_node[e];
-  if (node < 0 || a.owner[node] != e) return;  // not the owner
-  const F3 F = spread_take(a, node, e);
+  if (bump != nullptr && e == 0) {
+    bump->step += 1;
+    // populations that are not finite end the run as a bead NaN does
+    if (bump->pop_bad && bump->state == LBMD_RUNNING) bump->state = LBMD_NAN;
+  }
+  if (e >= nw) return;
+  const float4 v = src[e];
+  const int node = __float_as_int(v.w);
+  if (node < 0) return;  // not an owner
+  const F3 F{v.x, v.y, v.z};
   const size_t Vp = (size_t)g.Vp;
   uint32_t bb = 0u;
   int x = 0, y = 0, z = 0;
@@ -1049,24 +1083,28 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-cudaError_t launch_spread_accum(const ChainArgs &a, cudaStream_t s) {
+cudaError_t launch_spread_sum(const ChainArgs &a, cudaStream_t s) {
   if (a.N <= 0) return cudaSuccess;
-  k_spread_accum<<<(8 * a.N + 255) / 256, 256, 0, s>>>(a);
+  const int blocks = (8 * a.N + 255) / 256;
+  k_spread_accum<<<blocks, 256, 0, s>>>(a);
+  k_spread_finalize<<<blocks, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_spread_apply(int storage, const LbGeom &g, const ChainArgs &a, void *dst,
                                 int mode, DevStatus *bump, cudaStream_t s) {
-  const int blocks = a.N > 0 ? (8 * a.N + 255) / 256 : 1;
+  const int nw = a.sp_src ? 8 * a.N : 0;  // no records without a coupled chain
+  const int blocks = nw > 0 ? (nw + 255) / 256 : 1;
   switch (storage) {
     case LBMD_STORE_F32:
-      k_spread_apply<LBMD_STORE_F32><<<blocks, 256, 0, s>>>(g, a, (float *)dst, mode, bump);
+      k_spread_apply<LBMD_STORE_F32><<<blocks, 256, 0, s>>>(g, a.sp_src, nw, (float *)dst, mode, bump);
       break;
     case LBMD_STORE_F16:
-      k_spread_apply<LBMD_STORE_F16><<<blocks, 256, 0, s>>>(g, a, (__half *)dst, mode, bump);
+      k_spread_apply<LBMD_STORE_F16><<<blocks, 256, 0, s>>>(g, a.sp_src, nw, (__half *)dst, mode, bump);
       break;
     case LBMD_STORE_BF16:
-      k_spread_apply<LBMD_STORE_BF16><<<blocks, 256, 0, s>>>(g, a, (__nv_bfloat16 *)dst, mode, bump);
+      k_spread_apply<LBMD_STORE_BF16><<<blocks, 256, 0, s>>>(g, a.sp_src, nw, (__nv_bfloat16 *)dst, mode,
+                                                             bump);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -1075,7 +1113,7 @@ cudaError_t launch_spread_apply(int storage, const LbGeom &g, const ChainArgs &a
 }
 
 // Ensemble apply: same lane layout as k_ens_gather (the MD blocks have
-// accumulated the impulses).  The first lane of every realisation bumps its
+// summed the impulses into the owners' records).  The first lane of every realisation bumps its
 // step count (if live) and decides whether it takes part in the next step.
 template <int S>
 __global__ void __launch_bounds__(256)
@@ -1088,12 +1126,12 @@ __global__ void __launch_bounds__(256)
   int2 mi = make_int2(-1, 0);
   if (slot < nb) mi = beads[slot];
   const bool valid = mi.x >= 0 && live[mi.x];
-  if (valid) {
-    const ChainArgs &a = mem[mi.x].a;
-    const int ee = 8 * mi.y + k;
-    const int node = a.sp_node[ee];
-    if (node >= 0 && a.owner[node] == ee) {
-      const F3 F = spread_take(a, node, ee);
+  if (valid && mem[mi.x].a.sp_src) {
+    const float4 v = mem[mi.x].a.sp_src[8 * mi.y + k];
+    const int node = __float_as_int(v.w);
+    if (node >= 0) {  // the owner's record
+      const F3 F{v.x, v.y, v.z};
+      const ChainArgs &a = mem[mi.x].a;
       typename St::T *dst = (typename St::T *)mem[mi.x].pop[cur ^ 1];
       const size_t Vp = (size_t)a.geo.Vp;
       if (S == LBMD_STORE_F32) {
@@ -1118,6 +1156,7 @@ __global__ void __launch_bounds__(256)
       const long long s = st->step + 1;
       st->step = s;
       st->out_buf = cur ^ 1;
+      if (st->pop_bad && st->state == LBMD_RUNNING) st->state = LBMD_NAN;
       next = st->state == LBMD_RUNNING && s < *max_steps;
     }
     live_next[mi.x] = next;
@@ -1202,7 +1241,8 @@ __global__ void k_bead_block(const float4 *pos, const float4 *pos_lo, const floa
     w->step = st->step;
     w->t_transloc = st->t_transloc;
     w->n_trans = st->n_trans;
-    w->state = st->state;
+    // a box without beads has no apply kernel to fold the population flag in
+    w->state = st->state == LBMD_RUNNING && st->pop_bad ? LBMD_NAN : st->state;
   }
   if (i >= N) return;
   double *dpos = (double *)(out + kBeadBlockHeader), *dvel = dpos + 3 * (size_t)N;

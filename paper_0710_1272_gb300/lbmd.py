@@ -524,23 +524,34 @@ class Ensemble:
     """Many independent realisations (each a params dict with its own box,
     chain and seed; same storage and forcing) stepped together on the GPU.
 
-    ``init_pos[k]`` is the (N_k, 3) start of chain k.  The device workspace is
-    a torch uint8 tensor owned by this object."""
+    ``init_pos[k]`` is the (N_k, 3) start of chain k, or None for the
+    library's seeded start; ``init_vel``, ``init_rho`` and ``init_u`` are
+    optional lists of per-member arrays (entries may be None).  The device
+    workspace is a torch uint8 tensor owned by this object."""
 
-    def __init__(self, members, init_pos, device: str = "cuda", stream=None):
+    def __init__(self, members, init_pos=None, device: str = "cuda", stream=None, init_vel=None,
+                 init_rho=None, init_u=None):
         import torch
 
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
-        if len(members) != len(init_pos):
-            raise ValueError("one init_pos per member")
+        n = len(members)
+        per = []
+        for name, lst in (("init_pos", init_pos), ("init_vel", init_vel), ("init_rho", init_rho),
+                          ("init_u", init_u)):
+            if lst is None:
+                lst = [None] * n
+            if len(lst) != n:
+                raise ValueError(f"one {name} entry per member")
+            per.append(lst)
         self.p = [full_params(m) for m in members]
         self.count = len(self.p)
         self.device = torch.device(device)
         arr = (lbmd_params * self.count)()
         keep = []
-        for k, (m, pos) in enumerate(zip(self.p, init_pos)):
-            cp, kk = make_params(m, init_pos=pos)
+        for k, m in enumerate(self.p):
+            cp, kk = make_params(m, init_pos=per[0][k], init_vel=per[1][k], init_rho=per[2][k],
+                                 init_u=per[3][k])
             arr[k] = cp
             keep.append(kk)
         nbytes = lbmd_ensemble_workspace_size(arr)

@@ -96,10 +96,10 @@ def test_invalid_parameters_rejected(bad, msg):
     assert msg in str(e.value)
 
 
-def test_missing_bead_positions_rejected():
+def test_missing_bead_positions_take_the_seeded_start():
+    """init_pos == NULL is valid: the library draws its own start at create."""
     p = si.small_translocation(0, n_beads=4)
-    with pytest.raises(lb.LbmdError):
-        _ws(p)
+    assert _ws(p) == _ws(p, init_pos=si.saw_chain(p, 0))
 
 
 def test_non_chain_topology_unsupported():

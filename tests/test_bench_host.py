@@ -17,10 +17,10 @@ class _Args:
 
 def test_launches_per_step():
     p = bench.workload(0, "f32", _Args())
-    # gather, MD cycle, stream-collide, spread accumulate and apply
-    assert bench.launches_per_step(p) == 5
+    # gather, MD cycle, stream-collide, spread sum (two kernels) and apply
+    assert bench.launches_per_step(p) == 6
     p = bench.workload(0, "f16", _Args())
-    assert bench.launches_per_step(p) == 5
+    assert bench.launches_per_step(p) == 6
     a = _Args()
     a.workload = "solvent"
     assert bench.launches_per_step(bench.workload(0, "f32", a)) == 1

@@ -71,4 +71,17 @@ def test_noalloc_rejects_boxes_beyond_the_scratch():
     cp2, keep2 = lb.make_params(dict(nx=8, ny=8, nz=8, wall_x=-1))
     rc = L.lbmd_lb_step_noalloc(C.byref(cp2), C.c_void_p(f.data_ptr()), C.c_void_p(f.data_ptr()), None)
     assert rc == lb.lbmd.LBMD_EINVAL
-    del keep, keep2
+    # what the entry point does not cover: 16-bit storage, beads, the thermal source
+    for bad in (dict(storage="f16"), dict(kT_fluid=1e-4)):
+        cp3, keep3 = lb.make_params(dict(nx=8, ny=8, nz=8, wall_x=-1, **bad))
+        rc = L.lbmd_lb_step_noalloc(C.byref(cp3), C.c_void_p(f.data_ptr()), C.c_void_p(g.data_ptr()), None)
+        assert rc == lb.lbmd.LBMD_EUNSUPPORTED, bad
+    cp3.n_beads = 1
+    cp3.kT_fluid = 0.0
+    rc = L.lbmd_lb_step_noalloc(C.byref(cp3), C.c_void_p(f.data_ptr()), C.c_void_p(g.data_ptr()), None)
+    assert rc == lb.lbmd.LBMD_EUNSUPPORTED
+    # a box within the scratch whose y extent exceeds the launch grid
+    cp4, keep4 = lb.make_params(dict(nx=8, ny=600000, nz=1, wall_x=-1))
+    rc = L.lbmd_lb_step_noalloc(C.byref(cp4), C.c_void_p(f.data_ptr()), C.c_void_p(g.data_ptr()), None)
+    assert rc == lb.lbmd.LBMD_EINVAL
+    del keep, keep2, keep3, keep4
