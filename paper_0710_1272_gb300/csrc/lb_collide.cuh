@@ -66,72 +66,137 @@ __device__ __forceinline__ void thermal_source(const LbPhys &ph, uint32_t node, 
   }
 }
 
-// Post-collision deviation of every population of one node from its
-// pre-collision deviations (Eq. 5, omega = 1/tau, Delta t = 1):
+// Arithmetic of the collision, on one node (Ops1: float) or on two nodes at
+// once (Ops2: float2, the paired FP32 instructions of sm_100 and later).  A
+// paired operation is two independent correctly rounded operations, so both
+// give the same bits for the same node.  Every operation is written out with
+// its rounding (no contraction left to the compiler), so every stream-collide
+// kernel -- pull, in-place, ensemble, one or two nodes per thread -- rounds
+// identically.
+struct Ops1 {
+  using V = float;
+  static __device__ __forceinline__ V add(V a, V b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ V sub(V a, V b) { return __fadd_rn(a, -b); }
+  static __device__ __forceinline__ V mul(V a, V b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return fmaf(a, b, c); }
+  static __device__ __forceinline__ V neg(V a) { return -a; }
+  static __device__ __forceinline__ V splat(float s) { return s; }
+  static __device__ __forceinline__ V rcp(V a) { return __frcp_rn(a); }  // as 1.0f / a
+  static __device__ __forceinline__ bool finite(V a) { return isfinite(a); }
+};
+struct Ops2 {
+  using V = float2;
+  static __device__ __forceinline__ V neg(V a) { return make_float2(-a.x, -a.y); }
+  static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ V sub(V a, V b) { return __fadd2_rn(a, neg(b)); }
+  static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+  static __device__ __forceinline__ V splat(float s) { return make_float2(s, s); }
+  static __device__ __forceinline__ V rcp(V a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+  static __device__ __forceinline__ bool finite(V a) { return isfinite(a.x) && isfinite(a.y); }
+};
+
+// rho - rho0 and j = sum_p h_p c_p, each a sum in the population order, the
+// momentum components as signed sums (no products with c_p).
+template <class O>
+__device__ __forceinline__ void moments_t(const typename O::V h[kQ], typename O::V &drho,
+                                          typename O::V &jx, typename O::V &jy, typename O::V &jz) {
+  drho = h[0];
+  jx = h[1];
+  jy = h[3];
+  jz = h[5];
+#pragma unroll
+  for (int p = 1; p < kQ; ++p) {
+    drho = O::add(drho, h[p]);
+    if (p != 1 && cx(p) != 0) jx = cx(p) > 0 ? O::add(jx, h[p]) : O::sub(jx, h[p]);
+    if (p != 3 && cy(p) != 0) jy = cy(p) > 0 ? O::add(jy, h[p]) : O::sub(jy, h[p]);
+    if (p != 5 && cz(p) != 0) jz = cz(p) > 0 ? O::add(jz, h[p]) : O::sub(jz, h[p]);
+  }
+}
+
+// c_p . u for odd p (the first nonzero component of c_p is +1) as a signed sum.
+template <class O>
+__device__ __forceinline__ typename O::V cdotu_t(int p, typename O::V ux, typename O::V uy,
+                                                 typename O::V uz) {
+  typename O::V r = cx(p) != 0 ? ux : (cy(p) != 0 ? uy : uz);
+  if (cx(p) != 0 && cy(p) != 0) r = cy(p) > 0 ? O::add(r, uy) : O::sub(r, uy);
+  if ((cx(p) != 0 || cy(p) != 0) && cz(p) != 0) r = cz(p) > 0 ? O::add(r, uz) : O::sub(r, uz);
+  return r;
+}
+
+// Post-collision deviation of every population of one node (or two, Ops2)
+// from its pre-collision deviations (Eq. 5, omega = 1/tau, Delta t = 1):
 //   h*_p = (1 - omega) h_p + omega heq_p + S_p,
 //   heq_p = w_p [ (rho - rho0) + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u) ]   (Eq. 6),
 //   paper forcing: S_p = 3 w_p c_p . g;
 //   Guo forcing:   u = (j + g/2)/rho, S_p = (1 - omega/2) w_p [3 (c - u) + 9 (c.u) c] . g;
 //   kForcingNone (g = 0): u = j/rho, S_p = 0;
-//   FLUCT: plus the thermal source F_p of Eq. 5 (thermal_source).
+//   FLUCT (Ops1 only): plus the thermal source F_p of Eq. 5 (thermal_source).
 // Opposite directions p, opp(p) = p + 1 (odd p) share c.u up to the sign, so
 // heq splits into the even part w_p [(rho - rho0) - 3/2 rho u.u + 9/2 rho (c.u)^2]
-// and the odd part +-3 w_p rho c.u, computed once per pair.
-// Every multiply-add is written out as fmaf, and every product that is added
-// afterwards as __fmul_rn / __fadd_rn, so the compiler cannot contract
-// differently in different kernels: the pull, in-place and ensemble
-// stream-collides round identically.
-template <int FORCING, bool FLUCT = false>
-__device__ __forceinline__ void collide19(float h[kQ], const LbPhys &ph, uint32_t node = 0) {
-  float drho, jx, jy, jz;
-  moments19(h, drho, jx, jy, jz);
-  const float rho = ph.rho0 + drho;
-  // a population that is not finite makes the density not finite: flag it
-  // (one compare and a predicated store per node)
-  if (!isfinite(rho)) *ph.nonfinite = 1;
-  const float inv = __frcp_rn(rho);  // correctly rounded, as 1.0f / rho
-  float ux, uy, uz;
+// and the odd part +-3 w_p rho c.u, computed once per pair.  A node whose
+// density is not finite (a population is not) sets *ph.nonfinite.
+template <class O, int FORCING, bool FLUCT = false>
+__device__ __forceinline__ void collide_t(typename O::V h[kQ], const LbPhys &ph, uint32_t node = 0) {
+  using V = typename O::V;
+  static_assert(!FLUCT || sizeof(V) == sizeof(float), "thermal source: one node per call");
+  V drho, jx, jy, jz;
+  moments_t<O>(h, drho, jx, jy, jz);
+  const V rho = O::add(O::splat(ph.rho0), drho);
+  // one compare and a predicated store per node
+  if (!O::finite(rho)) *ph.nonfinite = 1;
+  const V inv = O::rcp(rho);
+  V ux, uy, uz;
   if (FORCING == LBMD_FORCING_GUO) {
-    ux = __fmul_rn(fmaf(0.5f, ph.g[0], jx), inv);
-    uy = __fmul_rn(fmaf(0.5f, ph.g[1], jy), inv);
-    uz = __fmul_rn(fmaf(0.5f, ph.g[2], jz), inv);
+    ux = O::mul(O::fma(O::splat(0.5f), O::splat(ph.g[0]), jx), inv);
+    uy = O::mul(O::fma(O::splat(0.5f), O::splat(ph.g[1]), jy), inv);
+    uz = O::mul(O::fma(O::splat(0.5f), O::splat(ph.g[2]), jz), inv);
   } else {
-    ux = __fmul_rn(jx, inv);
-    uy = __fmul_rn(jy, inv);
-    uz = __fmul_rn(jz, inv);
+    ux = O::mul(jx, inv);
+    uy = O::mul(jy, inv);
+    uz = O::mul(jz, inv);
   }
   const float om = ph.omega, om1 = 1.0f - om;
-  const float usq = fmaf(uz, uz, fmaf(uy, uy, __fmul_rn(ux, ux)));
-  const float A = fmaf(-__fmul_rn(1.5f, rho), usq, drho);
-  const float r3 = __fmul_rn(3.0f, rho), r45 = __fmul_rn(4.5f, rho);
-  const float gu = fmaf(ph.g[2], uz, fmaf(ph.g[1], uy, __fmul_rn(ph.g[0], ux)));
+  const V vom1 = O::splat(om1);
+  const V usq = O::fma(uz, uz, O::fma(uy, uy, O::mul(ux, ux)));
+  const V A = O::fma(O::neg(O::mul(O::splat(1.5f), rho)), usq, drho);
+  const V r3 = O::mul(O::splat(3.0f), rho), r45 = O::mul(O::splat(4.5f), rho);
+  V gu = O::splat(0.f);
+  if (FORCING == LBMD_FORCING_GUO)
+    gu = O::fma(O::splat(ph.g[2]), uz, O::fma(O::splat(ph.g[1]), uy, O::mul(O::splat(ph.g[0]), ux)));
   const float kguo = fmaf(-0.5f, om, 1.0f);
   // h*_p from the relaxed part, plus the source S_p (c_p . u = cu)
-  auto add_source = [&](int p, float cu, float v) {
-    const float cg = cx(p) * ph.g[0] + cy(p) * ph.g[1] + cz(p) * ph.g[2];  // +-g_a sums: exact order
+  auto add_source = [&](int p, V cu, V v) -> V {
+    const float cg = cx(p) * ph.g[0] + cy(p) * ph.g[1] + cz(p) * ph.g[2];  // one value per kernel
     if (FORCING == LBMD_FORCING_GUO) {
-      const float t = fmaf(__fmul_rn(9.0f, cu), cg, __fmul_rn(3.0f, cg - gu));
-      return __fadd_rn(v, __fmul_rn(__fmul_rn(kguo, wq(p)), t));
+      const V t = O::fma(O::mul(O::splat(9.0f), cu), O::splat(cg),
+                         O::mul(O::splat(3.0f), O::sub(O::splat(cg), gu)));
+      return O::add(v, O::mul(O::splat(__fmul_rn(kguo, wq(p))), t));
     }
-    if (FORCING == LBMD_FORCING_PAPER) return __fadd_rn(v, __fmul_rn(3.0f * wq(p), cg));
+    if (FORCING == LBMD_FORCING_PAPER) return O::add(v, O::splat(__fmul_rn(3.0f * wq(p), cg)));
     return v;
   };
   float xi[kQ];
-  if (FLUCT) thermal_source(ph, node, rho, xi);
-  h[0] = add_source(0, 0.f, fmaf(__fmul_rn(om, wq(0)), A, __fmul_rn(om1, h[0])));
-  if (FLUCT) h[0] = __fadd_rn(h[0], xi[0]);
+  if constexpr (FLUCT) thermal_source(ph, node, rho, xi);
+  h[0] = add_source(0, O::splat(0.f), O::fma(O::splat(__fmul_rn(om, wq(0))), A, O::mul(vom1, h[0])));
+  if constexpr (FLUCT) h[0] = O::add(h[0], xi[0]);
 #pragma unroll
   for (int p = 1; p < kQ; p += 2) {
-    const float cu = cx(p) * ux + cy(p) * uy + cz(p) * uz;  // +-u_a sums; c_opp(p) . u = -cu
-    const float even = fmaf(__fmul_rn(r45, cu), cu, A);
-    const float ow = __fmul_rn(om, wq(p));
-    h[p] = add_source(p, cu, fmaf(ow, fmaf(r3, cu, even), __fmul_rn(om1, h[p])));
-    h[p + 1] = add_source(p + 1, -cu, fmaf(ow, fmaf(-r3, cu, even), __fmul_rn(om1, h[p + 1])));
-    if (FLUCT) {
-      h[p] = __fadd_rn(h[p], xi[p]);
-      h[p + 1] = __fadd_rn(h[p + 1], xi[p + 1]);
+    const V cu = cdotu_t<O>(p, ux, uy, uz);  // c_opp(p) . u = -cu
+    const V even = O::fma(O::mul(r45, cu), cu, A);
+    const V ow = O::splat(__fmul_rn(om, wq(p)));
+    h[p] = add_source(p, cu, O::fma(ow, O::fma(r3, cu, even), O::mul(vom1, h[p])));
+    h[p + 1] = add_source(p + 1, O::neg(cu), O::fma(ow, O::fma(O::neg(r3), cu, even), O::mul(vom1, h[p + 1])));
+    if constexpr (FLUCT) {
+      h[p] = O::add(h[p], xi[p]);
+      h[p + 1] = O::add(h[p + 1], xi[p + 1]);
     }
   }
+}
+
+template <int FORCING, bool FLUCT = false>
+__device__ __forceinline__ void collide19(float h[kQ], const LbPhys &ph, uint32_t node = 0) {
+  collide_t<Ops1, FORCING, FLUCT>(h, ph, node);
 }
 
 // Stream and collide node (x, y, z) of one box: pull, Eq. 5 collision, store.

@@ -112,9 +112,10 @@ def test_nonfinite_populations_detected_one_step_later(storage):
 
 
 def test_nonfinite_populations_stop_a_coupled_box():
-    """gamma = 0: the chain feels no drag from the exploding flow (with drag,
-    its constraint solve fails first and the state is LBMD_SHAKE_FAIL), so a
-    NaN state can only come from the populations."""
+    """gamma = 0: the exploding flow drags no bead apart (with drag the
+    constraint solve fails first and the state is LBMD_SHAKE_FAIL); once the
+    populations are not finite the state is LBMD_NAN -- the beads may be
+    non-finite too, since u_i enters the drag force (0 * NaN is NaN)."""
     lb = _lb()
     p = si.small_translocation(1)
     p.update(tau=0.5001, lj_eps=PAPER_EPS, gamma=0.0)
@@ -127,8 +128,6 @@ def test_nonfinite_populations_stop_a_coupled_box():
             break
     assert sim.status()["state"] == lb.NAN
     assert not np.all(np.isfinite(sim.populations()))
-    r, v = sim.beads()
-    assert np.all(np.isfinite(r)) and np.all(np.isfinite(v))
 
 
 def test_ensemble_failing_members_stop_others_run_on():
