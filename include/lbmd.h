@@ -276,10 +276,13 @@ int lbmd_status(lbmd_ctx *ctx, int64_t *step, int32_t *n_trans, int32_t *state,
 int lbmd_solver_stats(lbmd_ctx *ctx, int32_t *newton_iters_last_step, int32_t *failed_steps);
 
 /*
- * Kernel timing for benchmarks: while enabled, lbmd_step launches kernels
- * directly (no graph) and brackets every stream-collide launch with CUDA
- * events on its stream.  lbmd_lb_kernel_time synchronises and returns the
- * summed duration (ms) and count of those launches since timing was enabled.
+ * Kernel timing for benchmarks: while enabled, each lbmd_step call captures
+ * its n_steps steps into one CUDA graph in which event-record nodes bracket
+ * every stream-collide (and the MD cycle and the spread apply), and launches
+ * it; the times are those of the graph's execution on the device.
+ * lbmd_lb_kernel_time synchronises and returns the summed duration (ms) and
+ * count of those stream-collide launches since timing was enabled.
+ * n_steps <= 2^20 per call while timing.
  */
 int lbmd_set_kernel_timing(lbmd_ctx *ctx, int enable);
 int lbmd_lb_kernel_time(lbmd_ctx *ctx, double *total_ms, int64_t *launches);
@@ -425,10 +428,14 @@ int lbmd_ensemble_read_diagnostics(lbmd_ensemble *ens, int32_t member, lbmd_diag
  * Launch shape of the ensemble stream-collide: tile height rows (4, 8 or 16
  * rows of 32 consecutive nodes), register budget for warps resident warps per
  * SM (32: 64 registers, or 48: 40 registers), tiles taken per claim of the
- * work counter (1 .. 64) and cells per thread (1, or 2: the nodes at the same
- * (x, y) on two consecutive z-planes, with warps = 32 and rows 4 or 8 only).
- * Default (8, 48, 2, 1).  The CUDA graphs are re-captured at the next step.
+ * work counter (1 .. 64) and cells per thread: 1; 2, the nodes at the same
+ * (x, y) on two consecutive z-planes; or LBMD_ENS_XPAIR, two x-adjacent
+ * nodes whose 16-bit deviations share one 32-bit word (16-bit storage only;
+ * tiles of 64 x rows nodes).  The two-cell shapes need warps = 32 and rows 4
+ * or 8.  Default (8, 48, 2, 1).  The CUDA graphs are re-captured at the next
+ * step.
  */
+#define LBMD_ENS_XPAIR 3
 int lbmd_ensemble_set_tuning(lbmd_ensemble *ens, int32_t rows, int32_t warps, int32_t claim,
                              int32_t cells_per_thread);
 int lbmd_ensemble_get_tuning(lbmd_ensemble *ens, int32_t *rows, int32_t *warps, int32_t *claim,
@@ -436,7 +443,7 @@ int lbmd_ensemble_get_tuning(lbmd_ensemble *ens, int32_t *rows, int32_t *warps, 
 
 /*
  * Autotuner: times the stream-collide alone, `trials` launches per shape, for
- * every shape above (cells per thread 1 or 2, rows, warps, claim in
+ * every shape above (cells per thread 1, 2 or LBMD_ENS_XPAIR, rows, warps, claim in
  * {1, 2, 4, 8}) on the live realisations' current populations, and keeps the
  * fastest.  The trial launches write exactly what the next step's
  * stream-collide writes (from the same input), so the simulation is

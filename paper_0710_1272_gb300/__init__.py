@@ -7,7 +7,7 @@ C ABI in ``include/lbmd.h``); :mod:`.lbmd` is its ctypes binding and
 realisations) are convenience wrappers that own a torch device workspace.
 """
 from .lbmd import (  # noqa: F401
-    COUPLING, FORCING, MAX_BEADS, NAN, RETRACTED, RUNNING, SHAKE_FAIL, STORAGE, STREAMING,
+    COUPLING, ENS_XPAIR, FORCING, MAX_BEADS, NAN, RETRACTED, RUNNING, SHAKE_FAIL, STORAGE, STREAMING,
     TRANSLOCATED, Ensemble, LbmdError, Simulation, bead_block_bytes, decode_bead_block,
     full_params, lbmd_create, lbmd_destroy,
     lbmd_kernel_times, lbmd_lb_kernel_time, lbmd_lb_step_noalloc, lbmd_read_bead_aux,

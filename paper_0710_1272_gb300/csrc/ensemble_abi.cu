@@ -170,6 +170,14 @@ void drop_graphs(lbmd_ensemble *e) {
       }
 }
 
+// Two x-adjacent nodes per thread need 16-bit storage and even rows.
+bool xpair_ok(const lbmd_ensemble *e) {
+  if (e->storage == LBMD_STORE_F32) return false;
+  for (const lbmd_params &p : e->p)
+    if (p.nx % 2) return false;
+  return true;
+}
+
 // Tile list of the realisations flagged in `live` for the current tile
 // height, uploaded on the private stream (synchronised before the host
 // vector can change again).
@@ -180,10 +188,13 @@ cudaError_t upload_tiles(lbmd_ensemble *e, const std::vector<int> &live) {
     if (!live[m]) continue;
     ++n_live;
     const lbmd_params &p = e->p[m];
-    const int plane = p.nx * p.ny, ts = 32 * e->rows;
-    for (int z0 = 0; z0 < p.nz; z0 += e->cpt)
+    // nodes per tile: 32 x rows (64 x rows for x-pairs), one plane (two for
+    // z-pairs)
+    const int plane = p.nx * p.ny, ts = (e->cpt == kEnsXPair ? 64 : 32) * e->rows;
+    const int dz = e->cpt == 2 ? 2 : 1;
+    for (int z0 = 0; z0 < p.nz; z0 += dz)
       for (int r0 = 0; r0 < plane; r0 += ts)
-        e->htiles.push_back(EnsTile{m, z0, r0, std::min(e->cpt, p.nz - z0)});
+        e->htiles.push_back(EnsTile{m, z0, r0, std::min(dz, p.nz - z0)});
   }
   const int n = (int)e->htiles.size();
   cudaError_t err;
@@ -466,9 +477,10 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
     EnsMember &M = e->hmem[m];
     memset(&M, 0, sizeof(M));
     M.a = e->inst[m].chain;
-    // the MD blocks of coupled chains sum the spread (beside the stream-collide);
-    // without a solvent there are no spread buffers (owner, acc, sp_src null)
-    M.a.md_accum = M.a.sp_src != nullptr ? 1 : 0;
+    // the MD blocks of coupled chains sum the spread (beside the stream-collide):
+    // in shared memory, or for chains longer than its table with global atomics;
+    // without a solvent there are no spread buffers (and md_accum is 0)
+    if (M.a.sp_src != nullptr && M.a.md_accum != kSumShared) M.a.md_accum = kSumGlobal;
     M.a.f = nullptr;
     M.a.f_mode = kPopPull;
     M.ph = e->inst[m].phys;
@@ -681,10 +693,12 @@ int lbmd_ensemble_set_tuning(lbmd_ensemble *e, int32_t rows, int32_t warps, int3
   if (rows != 4 && rows != 8 && rows != 16) return fail(LBMD_EINVAL, "rows must be 4, 8 or 16");
   if (warps != 32 && warps != 48) return fail(LBMD_EINVAL, "warps must be 32 or 48");
   if (claim < 1 || claim > 64) return fail(LBMD_EINVAL, "claim must be in [1, 64]");
-  if (cells_per_thread != 1 && cells_per_thread != 2)
-    return fail(LBMD_EINVAL, "cells_per_thread must be 1 or 2");
-  if (cells_per_thread == 2 && (warps != 32 || rows == 16))
+  if (cells_per_thread != 1 && cells_per_thread != 2 && cells_per_thread != kEnsXPair)
+    return fail(LBMD_EINVAL, "cells_per_thread must be 1, 2 or LBMD_ENS_XPAIR");
+  if (cells_per_thread != 1 && (warps != 32 || rows == 16))
     return fail(LBMD_EINVAL, "two cells per thread need warps = 32 and rows 4 or 8");
+  if (cells_per_thread == kEnsXPair && !xpair_ok(e))
+    return fail(LBMD_EINVAL, "x-adjacent pairs need 16-bit storage and an even nx in every member");
   EK(e, cudaStreamSynchronize(e->own));
   const bool retile = rows != e->rows || cells_per_thread != e->cpt;
   e->rows = rows;
@@ -735,8 +749,9 @@ int lbmd_ensemble_autotune(lbmd_ensemble *e, int32_t trials, double *best_ms) {
   cudaError_t err = cudaSuccess;
   std::vector<int> hl;
   if ((err = read_live(e, hl)) != cudaSuccess) goto done;
-  for (int cpt : {1, 2})
+  for (int cpt : {1, 2, kEnsXPair})
   for (int rows : {4, 8, 16}) {
+    if (cpt == kEnsXPair && !xpair_ok(e)) continue;
     e->rows = rows;
     e->cpt = cpt;
     if ((err = upload_tiles(e, hl)) != cudaSuccess) goto done;

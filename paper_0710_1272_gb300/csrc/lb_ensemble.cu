@@ -1,6 +1,8 @@
 // lb_ensemble.cu -- the ensemble stream-collide: one persistent kernel over
 // the tiles of every live realisation, and the dispatch over its launch
 // shapes for the autotuner.
+#include <type_traits>
+
 #include "lb_collide.cuh"
 
 namespace lbmd {
@@ -13,7 +15,10 @@ namespace lbmd {
 // updating the node of each plane at the same (x, y) with all 38 loads issued
 // before either collision -- so a warp reads and writes one contiguous run of
 // every population whatever the box width (no idle lanes for widths that are
-// not a multiple of 32).  A warp takes the bounce-back checks if any of its
+// not a multiple of 32).  With CPT = 3 (16-bit storage) a thread takes two
+// x-adjacent nodes instead, whose deviations share a 32-bit word (pair_node),
+// and a tile is 64 x ROWS consecutive nodes of one plane (every member's nx
+// is even, so a pair never straddles a row).  A warp takes the bounce-back checks if any of its
 // nodes needs them.  WARPS is the occupancy the register budget is sized for:
 // 48 warps per SM (40 registers, a little spilling) or 32 (64 registers,
 // none); population offsets are 32-bit.
@@ -65,7 +70,7 @@ __global__ void __launch_bounds__(32 * ROWS, WARPS / ROWS)
       // node of this thread: row-major index r in the plane, its row by a
       // float reciprocal with a one-step correction (exact for nx * ny < 2^22)
       const int plane = d.nx * d.ny;
-      const int r = w.z + tid;
+      const int r = w.z + (CPT == 3 ? 2 * tid : tid);
       const bool active = r < plane;
       int y = __float2int_rz((float)r * d.inv_nx);
       int x = r - y * d.nx;
@@ -78,7 +83,12 @@ __global__ void __launch_bounds__(32 * ROWS, WARPS / ROWS)
       }
       const T *src = (const T *)(cur ? d.pop[1] : d.pop[0]);
       T *dst = (T *)(cur ? d.pop[0] : d.pop[1]);
-      if (CPT == 2 && w.w == 2) {
+      if constexpr (CPT == 3) {
+        using T2 = typename std::conditional<S == LBMD_STORE_F16, __half2, __nv_bfloat162>::type;
+        const bool near = __any_sync(0xffffffffu, active && tile_is_near(g, x, y, w.y));
+        if (active)
+          pair_node<T2, FORCING>(g, ph, (const uint32_t *)src, (uint32_t *)dst, x >> 1, y, w.y, near);
+      } else if (CPT == 2 && w.w == 2) {
         const bool near = __any_sync(0xffffffffu, active && (tile_is_near(g, x, y, w.y) ||
                                                               tile_is_near(g, x, y, w.y + 1)));
         if (active) stream_collide_node2<S, FORCING>(g, ph, src, dst, x, y, w.y, near);
@@ -118,6 +128,14 @@ struct EnsLbFns {
 };
 template <int S, int F, int R>
 static EnsLbFns ens_fns_warps(int warps, int cpt) {
+  if (cpt == 3) {  // x-pairs: 16-bit storage, 64 registers, rows 4 or 8
+    if constexpr (S == LBMD_STORE_F32) {
+      return {nullptr, nullptr};
+    } else {
+      if (warps != 32 || R == 16) return {nullptr, nullptr};
+      return {&ens_lb_launch<S, F, R, 32, 3>, &ens_lb_occupancy<S, F, R, 32, 3>};
+    }
+  }
   if (cpt == 2) {
     if (warps != 32 || R == 16) return {nullptr, nullptr};
     return {&ens_lb_launch<S, F, R, 32, 2>, &ens_lb_occupancy<S, F, R, 32, 2>};

@@ -26,104 +26,20 @@ __global__ void __launch_bounds__(32 * kRowsPerBlock, 6)
   stream_collide_node<S, FORCING, I>(g, ph, src, dst, x, y, z, tile_is_near(g, x, y, z));
 }
 
-// 16-bit storage: one thread per pair of x-adjacent nodes (2i, 2i + 1), whose
-// deviations of one population share a 32-bit word (nx even, so a pair never
-// straddles a row).  Every population is one 32-bit load for c_x = 0 and two
-// for c_x = +-1 (the neighbouring word supplies the shifted half; one byte
-// permute assembles the pair), one 32-bit store, and the collision runs once
-// for both nodes on float2 with the paired FP32 instructions: about half the
-// instructions per node of k_stream_collide, with the same bits.  A warp
-// covers 64 nodes of one row, i.e. two 32-node tiles; it takes the link-mask
-// path if either is near a solid node.  Words are indexed in 32 bits
-// (19 Vp < 2^31).
-template <typename T2> struct Pair16;
-template <> struct Pair16<__half2> {
-  static __device__ __forceinline__ float2 unpack(uint32_t w) {
-    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
-  }
-  static __device__ __forceinline__ uint32_t pack(float2 v) {
-    const __half2 h = __float22half2_rn(v);
-    return *reinterpret_cast<const uint32_t *>(&h);
-  }
-};
-template <> struct Pair16<__nv_bfloat162> {
-  static __device__ __forceinline__ float2 unpack(uint32_t w) {
-    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
-  }
-  static __device__ __forceinline__ uint32_t pack(float2 v) {
-    const __nv_bfloat162 h = __float22bfloat162_rn(v);
-    return *reinterpret_cast<const uint32_t *>(&h);
-  }
-};
-
-// Register budget: 64 (four blocks per SM) for the benchmark's zero-force
-// collision, 80 (three) for the forced variants, which would spill at 64.
+// 16-bit storage: one thread per pair of x-adjacent nodes (pair_node).  A
+// warp covers 64 nodes of one row, i.e. two 32-node tiles.  Register budget:
+// 64 (four blocks per SM) for the benchmark's zero-force collision, 80 (three)
+// for the forced variants, which would spill at 64.
 template <typename T2, int FORCING>
 __global__ void __launch_bounds__(32 * kRowsPerBlock, FORCING == kForcingNone ? 4 : 3)
     k_stream_collide_pair(LbGeom g, LbPhys ph, const uint32_t *__restrict__ src,
                           uint32_t *__restrict__ dst, DevStatus *bump) {
-  using P = Pair16<T2>;
   const int xw = blockIdx.x * 32 + threadIdx.x;  // word: nodes 2 xw, 2 xw + 1
   const int y = blockIdx.y * kRowsPerBlock + threadIdx.y;
   const int z = blockIdx.z;
   if (bump != nullptr && xw == 0 && y == 0 && z == 0) bump->step += 1;
-  const int wpr = g.nx >> 1;  // words per row
-  if (xw >= wpr || y >= g.ny) return;
-  const int Vw = (int)(g.Vp >> 1);
-  const int ny = g.ny;
-  const int self = (z * ny + y) * wpr + xw;
-  const bool near = tile_is_near(g, 2 * xw, y, z);
-  // link masks of the two nodes (bit 0: solid; bit p: the pull source is solid)
-  uint2 bb = make_uint2(0u, 0u);
-  if (near) bb = __ldg(reinterpret_cast<const uint2 *>(g.lmask) + self);
-  if ((bb.x & bb.y) & 1u) return;  // both solid: nothing to write
-  const int ym = wrap_m1(y, ny), yp = wrap_p1(y, ny);
-  const int zm = wrap_m1(z, g.nz), zp = wrap_p1(z, g.nz);
-  const int xl = xw == 0 ? wpr - 1 : xw - 1, xr = xw == wpr - 1 ? 0 : xw + 1;
-  float2 h[kQ];
-#pragma unroll
-  for (int p = 0; p < kQ; ++p) {
-    // source row of x - c_p; the pair's sources are x - c_x, x - c_x + 1
-    const int sy = cy(p) == 1 ? ym : (cy(p) == -1 ? yp : y);
-    const int sz = cz(p) == 1 ? zm : (cz(p) == -1 ? zp : z);
-    const uint32_t *rowp = src + p * Vw + (sz * ny + sy) * wpr;
-    const uint32_t w0 = __ldg(rowp + xw);
-    uint32_t w = w0;
-    if (cx(p) == 1) w = __byte_perm(__ldg(rowp + xl), w0, 0x5432);   // (x - 1, x)
-    if (cx(p) == -1) w = __byte_perm(w0, __ldg(rowp + xr), 0x5432);  // (x + 1, x + 2)
-    h[p] = P::unpack(w);
-  }
-  if (near) {
-    // halfway bounce-back: a population whose source is solid comes back as
-    // the node's own post-collision opposite population
-#pragma unroll
-    for (int p = 1; p < kQ; ++p) {
-      const bool ba = (bb.x >> p) & 1u, bbb = (bb.y >> p) & 1u;
-      if (ba || bbb) {
-        const float2 r = P::unpack(__ldg(src + opp(p) * Vw + self));
-        if (ba) h[p].x = r.x;
-        if (bbb) h[p].y = r.y;
-      }
-    }
-    // a solid node of the pair: harmless inputs, and zero written back
-    if (bb.x & 1u)
-#pragma unroll
-      for (int p = 0; p < kQ; ++p) h[p].x = 0.f;
-    if (bb.y & 1u)
-#pragma unroll
-      for (int p = 0; p < kQ; ++p) h[p].y = 0.f;
-  }
-  collide_t<Ops2, FORCING>(h, ph);
-  if (near) {
-    if (bb.x & 1u)
-#pragma unroll
-      for (int p = 0; p < kQ; ++p) h[p].x = 0.f;
-    if (bb.y & 1u)
-#pragma unroll
-      for (int p = 0; p < kQ; ++p) h[p].y = 0.f;
-  }
-#pragma unroll
-  for (int p = 0; p < kQ; ++p) dst[p * Vw + self] = P::pack(h[p]);
+  if (xw >= (g.nx >> 1) || y >= g.ny) return;
+  pair_node<T2, FORCING>(g, ph, src, dst, xw, y, z, tile_is_near(g, 2 * xw, y, z));
 }
 
 template <typename T2>

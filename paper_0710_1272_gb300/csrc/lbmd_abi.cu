@@ -39,6 +39,7 @@ struct lbmd_ctx {
   int timing;
   std::vector<cudaEvent_t> tev;  // per timed step: lb, md, spread start/stop pairs
   size_t tev_used;
+  std::vector<cudaGraphExec_t> tgraphs;  // graphs of timed steps, destroyed once collected
   double timed_ms[3];            // summed durations of stream-collide, MD, spread
   long long timed_count;
   DevStatus *status;
@@ -70,6 +71,12 @@ int pop_mode(const lbmd_ctx *c, int src) {
   return c->aa ? (src ? kPopAASwap : kPopAALocal) : kPopPull;
 }
 
+// A timing event: captured into a step graph as an event-record node, so that
+// the recorded times are those of the graph's execution.
+cudaError_t record_timing(cudaEvent_t ev, cudaStream_t s) {
+  return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+}
+
 // Enqueue one coupled LB step reading pop[src] and writing pop[1 - src] (with
 // in-place streaming: the one buffer, even step if src = 0, odd if 1) on the
 // private stream `own`: the MD cycle (gather + M substeps) on the side stream
@@ -83,28 +90,23 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
   cudaError_t e;
   cudaEvent_t t[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   if (c->timing) {
-    if (c->tev_used + 6 > c->tev.size()) {
-      for (int k = 0; k < 600; ++k) {
-        cudaEvent_t ev;
-        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
-        c->tev.push_back(ev);
-      }
-    }
+    // events reserved by lbmd_step before the capture
+    if (c->tev_used + 6 > c->tev.size()) return cudaErrorInvalidValue;
     for (int k = 0; k < 6; ++k) t[k] = c->tev[c->tev_used + k];
     c->tev_used += 6;
   }
   if (c->p.solvent_free) {
     // no solvent (u_i stays 0): the M MD substeps, then the spread, which
     // finds no transfer node and only advances the step counter
-    if (t[2] && (e = cudaEventRecord(t[2], c->own)) != cudaSuccess) return e;
+    if (t[2] && (e = record_timing(t[2], c->own)) != cudaSuccess) return e;
     if ((e = launch_md_cycle(c->chain, c->prio_high, c->own)) != cudaSuccess) return e;
-    if (t[3] && (e = cudaEventRecord(t[3], c->own)) != cudaSuccess) return e;
+    if (t[3] && (e = record_timing(t[3], c->own)) != cudaSuccess) return e;
     for (int k : {0, 1, 4})
-      if (t[k] && (e = cudaEventRecord(t[k], c->own)) != cudaSuccess) return e;
+      if (t[k] && (e = record_timing(t[k], c->own)) != cudaSuccess) return e;
     if ((e = launch_spread_apply(c->p.storage, c->geo, c->chain, B, mode_out, c->status, c->own)) !=
         cudaSuccess)
       return e;
-    if (t[5] && (e = cudaEventRecord(t[5], c->own)) != cudaSuccess) return e;
+    if (t[5] && (e = record_timing(t[5], c->own)) != cudaSuccess) return e;
     return cudaSuccess;
   }
   if (c->N > 0) {
@@ -113,19 +115,19 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     ChainArgs a = c->chain;
     a.f = A;
     a.f_mode = pop_mode(c, src);
-    if (t[2] && (e = cudaEventRecord(t[2], c->own)) != cudaSuccess) return e;
+    if (t[2] && (e = record_timing(t[2], c->own)) != cudaSuccess) return e;
     if ((e = launch_gather(c->p.storage, a, c->own)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(c->ev_fork, c->own)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(c->side, c->ev_fork, 0)) != cudaSuccess) return e;
     if ((e = launch_md_cycle(a, c->prio_high, c->side)) != cudaSuccess) return e;
-    if (t[3] && (e = cudaEventRecord(t[3], c->side)) != cudaSuccess) return e;
+    if (t[3] && (e = record_timing(t[3], c->side)) != cudaSuccess) return e;
     // sum part of the spread, beside the stream-collide
     if ((e = launch_spread_sum(c->chain, c->side)) != cudaSuccess) return e;
   } else if (t[2]) {
-    if ((e = cudaEventRecord(t[2], c->own)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(t[3], c->own)) != cudaSuccess) return e;
+    if ((e = record_timing(t[2], c->own)) != cudaSuccess) return e;
+    if ((e = record_timing(t[3], c->own)) != cudaSuccess) return e;
   }
-  if (t[0] && (e = cudaEventRecord(t[0], c->own)) != cudaSuccess) return e;
+  if (t[0] && (e = record_timing(t[0], c->own)) != cudaSuccess) return e;
   DevStatus *bump = c->N > 0 ? nullptr : c->status;
   if (c->phys.step) {
     // thermal source: the kernel reads the step count, so a box without
@@ -139,18 +141,18 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
               : launch_lb_stream_collide(c->p.storage, c->geo, c->phys, A, B, bump, c->own);
     if (e != cudaSuccess) return e;
   }
-  if (t[1] && (e = cudaEventRecord(t[1], c->own)) != cudaSuccess) return e;
+  if (t[1] && (e = record_timing(t[1], c->own)) != cudaSuccess) return e;
   if (c->N > 0) {
     if ((e = cudaEventRecord(c->ev_join, c->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(c->own, c->ev_join, 0)) != cudaSuccess) return e;
-    if (t[4] && (e = cudaEventRecord(t[4], c->own)) != cudaSuccess) return e;
+    if (t[4] && (e = record_timing(t[4], c->own)) != cudaSuccess) return e;
     if ((e = launch_spread_apply(c->p.storage, c->geo, c->chain, B, mode_out, c->status, c->own)) !=
         cudaSuccess)
       return e;
-    if (t[5] && (e = cudaEventRecord(t[5], c->own)) != cudaSuccess) return e;
+    if (t[5] && (e = record_timing(t[5], c->own)) != cudaSuccess) return e;
   } else if (t[4]) {
-    if ((e = cudaEventRecord(t[4], c->own)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(t[5], c->own)) != cudaSuccess) return e;
+    if ((e = record_timing(t[4], c->own)) != cudaSuccess) return e;
+    if ((e = record_timing(t[5], c->own)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -186,6 +188,7 @@ void destroy_ctx(lbmd_ctx *c) {
   for (auto &row : c->graph)
     for (auto &gx : row)
       if (gx) cudaGraphExecDestroy(gx);
+  for (cudaGraphExec_t ex : c->tgraphs) cudaGraphExecDestroy(ex);
   for (cudaEvent_t ev : c->tev) cudaEventDestroy(ev);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
@@ -303,15 +306,21 @@ int lbmd_step(lbmd_ctx *c, int64_t n_steps) {
   if (n_steps == 0) return LBMD_OK;
   c->status_fresh = 0;
   if (c->timing) {
-    // direct launches on the private streams, joined back into the caller's
-    CK(c, cudaEventRecord(c->ev_in, c->user));
-    CK(c, cudaStreamWaitEvent(c->own, c->ev_in, 0));
-    for (int64_t k = 0; k < n_steps; ++k) {
-      CK(c, enqueue_step(c, c->cur));
-      c->cur ^= 1;
+    // the n steps captured into one graph with event-record nodes around the
+    // kernels (six events per step, reserved here), launched into the
+    // caller's stream like the step graphs; kept until the times are read
+    if (n_steps > (1 << 20)) return fail(LBMD_EINVAL, "at most 2^20 timed steps per call");
+    const size_t need = c->tev_used + 6 * (size_t)n_steps;
+    while (c->tev.size() < need) {
+      cudaEvent_t ev;
+      CK(c, cudaEventCreate(&ev));
+      c->tev.push_back(ev);
     }
-    CK(c, cudaEventRecord(c->ev_out, c->own));
-    CK(c, cudaStreamWaitEvent(c->user, c->ev_out, 0));
+    cudaGraphExec_t ex = nullptr;
+    CK(c, capture(c, c->cur, (int)n_steps, &ex));
+    c->tgraphs.push_back(ex);
+    CK(c, cudaGraphLaunch(ex, c->user));
+    if (n_steps & 1) c->cur ^= 1;
     return LBMD_OK;
   }
   // graphs (captured on the private streams) launch straight into the
@@ -487,7 +496,10 @@ int lbmd_solver_stats(lbmd_ctx *c, int32_t *newton_iters_last_step, int32_t *fai
 int lbmd_set_kernel_timing(lbmd_ctx *c, int enable) {
   int rc = check_ctx(c);
   if (rc) return rc;
+  CK(c, cudaStreamSynchronize(c->user));
   CK(c, cudaStreamSynchronize(c->own));
+  for (cudaGraphExec_t ex : c->tgraphs) cudaGraphExecDestroy(ex);
+  c->tgraphs.clear();
   c->timing = enable ? 1 : 0;
   c->tev_used = 0;
   c->timed_ms[0] = c->timed_ms[1] = c->timed_ms[2] = 0;
@@ -496,8 +508,11 @@ int lbmd_set_kernel_timing(lbmd_ctx *c, int enable) {
 }
 
 static int collect_times(lbmd_ctx *c) {
+  CK(c, cudaStreamSynchronize(c->user));
   CK(c, cudaStreamSynchronize(c->own));
   CK(c, cudaStreamSynchronize(c->side));
+  for (cudaGraphExec_t ex : c->tgraphs) cudaGraphExecDestroy(ex);
+  c->tgraphs.clear();
   for (size_t k = 0; k + 5 < c->tev_used; k += 6) {
     for (int q = 0; q < 3; ++q) {
       float ms = 0.f;

@@ -45,7 +45,7 @@ size_t stage_floats_for(const lbmd_params &p) {
   return std::max((size_t)19 * (size_t)chunk_cells_for(p), (size_t)6 * Np * 2 + 8);
 }
 
-Layout make_layout(const lbmd_params &p, bool with_stage) {
+Layout make_layout(const lbmd_params &p, bool single_box) {
   Layout L{};
   const long long V = (long long)p.nx * p.ny * p.nz;
   L.Vp = (V + 63) / 64 * 64;
@@ -53,7 +53,7 @@ Layout make_layout(const lbmd_params &p, bool with_stage) {
   const size_t rows = (size_t)p.ny * p.nz;
   const size_t Np = (size_t)std::max(p.n_beads, 1);
   L.chunk_cells = chunk_cells_for(p);
-  L.stage_floats = with_stage ? stage_floats_for(p) : 0;
+  L.stage_floats = single_box ? stage_floats_for(p) : 0;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t at = o;
@@ -82,14 +82,16 @@ Layout make_layout(const lbmd_params &p, bool with_stage) {
   L.lam = take(Np * sizeof(float));
   L.status = take(sizeof(DevStatus));
   L.diag = take((size_t)std::max(p.diag_capacity, 0) * sizeof(DevDiag));
-  // a chain coupled to the solvent: the spread owner of every node (4 bytes
-  // per node), the fixed-point impulse sums and the apply records of the 8 N
-  // transfer entries
+  // a chain coupled to the solvent: the apply records of the 8 N transfer
+  // entries; unless an ensemble's MD block sums the chain in shared memory,
+  // also the spread owner of every node (4 bytes per node) and the
+  // fixed-point sums
   const bool coupled = p.n_beads > 0 && !p.solvent_free;
-  L.owner = coupled ? take((size_t)V * sizeof(int)) : 0;
-  L.acc = coupled ? take(8 * Np * sizeof(SpreadAcc)) : 0;
+  const bool global_sum = coupled && (single_box || p.n_beads > kSumSharedMaxN);
+  L.owner = global_sum ? take((size_t)V * sizeof(int)) : 0;
+  L.acc = global_sum ? take(8 * Np * sizeof(SpreadAcc)) : 0;
   L.sp_src = coupled ? take(8 * Np * sizeof(float4)) : 0;
-  L.stage = with_stage ? take(L.stage_floats * sizeof(float)) : 0;
+  L.stage = single_box ? take(L.stage_floats * sizeof(float)) : 0;
   L.total = o;
   return L;
 }
@@ -453,16 +455,20 @@ cudaError_t init_instance(const lbmd_params &p, const Layout &L, char *ws, cudaS
   UP(cudaMemcpyAsync(out.status, &st, sizeof(st), cudaMemcpyHostToDevice, s), "upload");
   ChainArgs &a = out.chain;
   a = ChainArgs{};
+  const size_t ne = 8 * (size_t)std::max(p.n_beads, 1);
+  if (L.sp_src) {
+    // apply records without a node (-1); the MD block sums the spread of
+    // chains that fit its shared table, two kernels that of longer ones
+    a.sp_src = (float4 *)(ws + L.sp_src);
+    UP(cudaMemsetAsync(a.sp_src, 0xff, ne * sizeof(float4), s), "memset");
+    a.md_accum = L.owner ? kSumKernels : kSumShared;
+  }
   if (L.owner) {
-    // spread owners at rest (every byte 0x7f = kOwnerFree), impulse sums zero,
-    // apply records without a node (-1)
-    const size_t ne = 8 * (size_t)std::max(p.n_beads, 1);
+    // spread owners at rest (every byte 0x7f = kOwnerFree), impulse sums zero
     a.owner = (int *)(ws + L.owner);
     a.acc = (SpreadAcc *)(ws + L.acc);
-    a.sp_src = (float4 *)(ws + L.sp_src);
     UP(cudaMemsetAsync(a.owner, 0x7f, (size_t)g.V * sizeof(int), s), "memset");
     UP(cudaMemsetAsync(a.acc, 0, ne * sizeof(SpreadAcc), s), "memset");
-    UP(cudaMemsetAsync(a.sp_src, 0xff, ne * sizeof(float4), s), "memset");
   }
   a.geo = g;
   a.has_wall = p.wall_x >= 0;

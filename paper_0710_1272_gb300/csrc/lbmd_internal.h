@@ -111,11 +111,14 @@ struct ChainArgs {
   int *sp_node;             // [8N] grid node of each transfer weight, -1 none
   float *sp_w;              // [8N] renormalised transfer weights
   int *owner;               // [V] per node: smallest transfer entry of this step
-                            // that hits it (kOwnerFree at rest)
+                            // that hits it (kOwnerFree at rest); kSumKernels and
+                            // kSumGlobal only
   SpreadAcc *acc;           // [8N] impulse sums, at the owner entry of each node
-  float4 *sp_src;           // [8N] per entry: at a node's owner (F_x, F_y, F_z, node)
-                            // with F the node's summed force; elsewhere node = -1
-  int md_accum;             // 1: the MD block sums the impulses itself
+                            // (kSumKernels and kSumGlobal only)
+  float4 *sp_src;           // [8N] apply records (F_x, F_y, F_z, node) of the
+                            // transfer nodes, F the node's summed force; unused
+                            // records have node = -1
+  int md_accum;             // how the spread is summed (kSum*)
   const double *b0;         // [N-1] bond lengths
   int *nl_cnt, *wl_cnt;     // [N] list lengths
   short *nl_list;           // [N][kMaxPairs] partner beads
@@ -211,13 +214,25 @@ cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s);
 //  - sum (any time after the MD cycle; all contributions to a box come from
 //    its one chain): every entry adds its share -w J_i of the impulse to
 //    acc[owner] in 64-bit fixed point; then each owner converts its sum once
-//    into sp_src[owner] = (F, node), and returns acc and owner[node] to rest;
+//    into sp_src[owner] = (F, node), and returns acc and owner[node] to rest
+//    (kSumShared: the same sums in a shared-memory table, below);
 //  - apply (after the stream-collide): each owner entry adds the source
 //    S_p = 3 w_p c_p . F to its node's post-collision populations of `dst` in
 //    layout `mode` -- the only write to those words.
 // launch_spread_sum enqueues the sum as two kernels (chains whose MD block
 // sums instead have md_accum set).
+// A single box sums with the owner field and global atomics in two kernels
+// after the MD cycle (kSumKernels: spread over many SMs, whose global memory
+// traffic is fast even while the stream-collide saturates HBM).  In an
+// ensemble, whose MD blocks run beside a far longer stream-collide, each MD
+// block sums its own chain after its last substep: for chains of up to
+// kSumSharedMaxN beads in a hash table of the chain's transfer nodes kept in
+// its (then free) shared memory (kSumShared: 64-bit fixed-point shared
+// atomics, no owner field; the records sit at the table's slots), for longer
+// ones with the owner field and global atomics (kSumGlobal).
 constexpr int kOwnerFree = 0x7f7f7f7f;
+constexpr int kSumKernels = 0, kSumGlobal = 1, kSumShared = 2;
+constexpr int kSumSharedMaxN = 512;
 cudaError_t launch_spread_sum(const ChainArgs &a, cudaStream_t s);
 // `bump` (may be null): status->step += 1 by one thread.
 cudaError_t launch_spread_apply(int storage, const LbGeom &g, const ChainArgs &a, void *dst,
@@ -230,8 +245,11 @@ cudaError_t launch_spread_apply(int storage, const LbGeom &g, const ChainArgs &a
 // gather).  Every realisation must have 19 Vp < 2^31 (32-bit offsets) and
 // nx * ny < 2^22 (float row division).
 // forcing: LBMD_FORCING_* or kForcingNone (every realisation has g = 0).
-// cpt: cells per thread, 1 or 2 (two consecutive z-planes; warps 32 and rows
-// 4 or 8 only -- other shapes are cudaErrorInvalidValue).
+// cpt: cells per thread, 1; 2 (two consecutive z-planes); or kEnsXPair (two
+// x-adjacent nodes sharing a 32-bit word, 16-bit storage).  The two-cell
+// shapes need warps 32 and rows 4 or 8 -- other shapes are
+// cudaErrorInvalidValue.
+constexpr int kEnsXPair = LBMD_ENS_XPAIR;
 cudaError_t launch_ens_stream_collide(int storage, int forcing, int rows, int warps, int cpt,
                                       int claim, int grid, const EnsLb *lbd, const EnsTile *tiles,
                                       const int *n_tiles, int *counter, const int *live, int cur,

@@ -516,8 +516,31 @@ __device__ F3 wall_stencil_forces(const ChainArgs &a, float4 rh, float4 rl) {
 
 // Fixed point of the spread: units of 2^-40.  The impulses of a node (|F| of
 // order 1e-2) keep ~30 significant bits, far below a float ulp of the
-// populations they reach.
+// populations they reach.  The conversions are built from 32-bit ones: 64-bit
+// integer <-> float conversions run at a small fraction of the FP32 rate on
+// this GPU.
 constexpr float kFixOne = 1099511627776.0f;  // 2^40
+
+// round(v 2^40) for |v| < 2^10 as a 64-bit integer, rounded to nearest even
+// like the direct conversion: with a = |v| 2^8 = hi + f (hi integral,
+// 0 <= f <= 1 - 2^-24; a, hi and f exact in float), |v| 2^40 = hi 2^32 +
+// f 2^32, only f 2^32 (< 2^32) needs rounding, and rounding to nearest even
+// is symmetric in the sign.
+__device__ __forceinline__ long long fix40(float v) {
+  const float a = fabsf(v) * 256.0f;
+  const float hi = floorf(a);
+  const unsigned lo = __float2uint_rn((a - hi) * 4294967296.0f);
+  const long long m = (long long)(((unsigned long long)__float2uint_rn(hi) << 32) | lo);
+  return v < 0.f ? -m : m;
+}
+
+// q 2^-40 as a float: hi 2^-8 + lo 2^-40 with q = hi 2^32 + lo (0 <= lo <
+// 2^32), the low word rounded to float first and the sum rounded once more.
+__device__ __forceinline__ float unfix40(long long q) {
+  const int hi = (int)(q >> 32);
+  const unsigned lo = (unsigned)(unsigned long long)q;
+  return __fmaf_rn((float)hi, 1.0f / 256.0f, __uint2float_rn(lo) * (1.0f / kFixOne));
+}
 
 // Adds entry e's share -w_e J_i of the impulse to the sum at the owner of its
 // node (64-bit integer atomics: the result does not depend on their order).
@@ -536,9 +559,9 @@ __device__ __forceinline__ void spread_add(const ChainArgs &a, int e, float4 j) 
     atomicOr(reinterpret_cast<unsigned long long *>(&q->bad), 1ull);
     return;
   }
-  atomicAdd(reinterpret_cast<unsigned long long *>(&q->x), (unsigned long long)__float2ll_rn(fx * kFixOne));
-  atomicAdd(reinterpret_cast<unsigned long long *>(&q->y), (unsigned long long)__float2ll_rn(fy * kFixOne));
-  atomicAdd(reinterpret_cast<unsigned long long *>(&q->z), (unsigned long long)__float2ll_rn(fz * kFixOne));
+  atomicAdd(reinterpret_cast<unsigned long long *>(&q->x), (unsigned long long)fix40(fx));
+  atomicAdd(reinterpret_cast<unsigned long long *>(&q->y), (unsigned long long)fix40(fy));
+  atomicAdd(reinterpret_cast<unsigned long long *>(&q->z), (unsigned long long)fix40(fz));
 }
 
 // The owner's conversion: the summed force of node `node` (NaN if a
@@ -554,8 +577,7 @@ __device__ __forceinline__ F3 spread_take(const ChainArgs &a, int node, int e) {
     const float nan = __int_as_float(0x7fc00000);
     return F3{nan, nan, nan};
   }
-  const float s = 1.0f / kFixOne;
-  return F3{__ll2float_rn(x) * s, __ll2float_rn(y) * s, __ll2float_rn(z) * s};
+  return F3{unfix40(x), unfix40(y), unfix40(z)};
 }
 
 // After every contribution is summed: entry e's record for the apply --
@@ -568,6 +590,64 @@ __device__ __forceinline__ void spread_finalize(const ChainArgs &a, int e) {
     out = make_float4(F.x, F.y, F.z, __int_as_float(node));
   }
   a.sp_src[e] = out;
+}
+
+// The spread sum of one chain in its MD block (kSumShared), after the last
+// substep: an open-addressing hash table of the chain's transfer nodes in the
+// block's dynamic shared memory (8 N slots: room for every entry), 64-bit
+// fixed-point shared atomics per node, then one record per slot.  Which slot a
+// node lands in depends on the order of the atomics; its sum does not.
+struct __align__(8) SpreadSlot {
+  int node, bad;
+  long long x, y, z;
+};
+
+__device__ __forceinline__ void spread_sum_shared(const ChainArgs &a, void *smem, bool bead, int i,
+                                                  F3 J) {
+  SpreadSlot *T = reinterpret_cast<SpreadSlot *>(smem);
+  const unsigned S = 8u * (unsigned)a.N;
+  __syncthreads();  // every read of the substep arrays is done
+  for (unsigned s = threadIdx.x; s < S; s += blockDim.x) T[s] = SpreadSlot{-1, 0, 0, 0, 0};
+  __syncthreads();
+  if (bead) {
+    int node[8];
+    float w[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      node[k] = a.sp_node[8 * i + k];
+      w[k] = a.sp_w[8 * i + k];
+    }
+    const float lim = 1024.0f;  // as spread_add: a larger share marks the sum
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (node[k] < 0) continue;
+      unsigned h = ((unsigned)node[k] * 2654435761u) % S;
+      for (;;) {  // at most S probes: the table has a slot for every entry
+        const int old = atomicCAS(&T[h].node, -1, node[k]);
+        if (old == -1 || old == node[k]) break;
+        h = h + 1 == S ? 0 : h + 1;
+      }
+      const float fx = -w[k] * J.x, fy = -w[k] * J.y, fz = -w[k] * J.z;
+      if (!(fabsf(fx) < lim && fabsf(fy) < lim && fabsf(fz) < lim)) {
+        atomicOr(&T[h].bad, 1);
+        continue;
+      }
+      atomicAdd(reinterpret_cast<unsigned long long *>(&T[h].x), (unsigned long long)fix40(fx));
+      atomicAdd(reinterpret_cast<unsigned long long *>(&T[h].y), (unsigned long long)fix40(fy));
+      atomicAdd(reinterpret_cast<unsigned long long *>(&T[h].z), (unsigned long long)fix40(fz));
+    }
+  }
+  __syncthreads();
+  for (unsigned s = threadIdx.x; s < S; s += blockDim.x) {
+    const SpreadSlot t = T[s];
+    float4 r = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+    if (t.node >= 0) {
+      const float nan = __int_as_float(0x7fc00000);
+      r = t.bad ? make_float4(nan, nan, nan, __int_as_float(t.node))
+                : make_float4(unfix40(t.x), unfix40(t.y), unfix40(t.z), __int_as_float(t.node));
+    }
+    a.sp_src[s] = r;
+  }
 }
 
 // (2) the M MD substeps of one chain, one thread per bead, and (5) the
@@ -771,17 +851,18 @@ __device__ __forceinline__ void md_cycle_body(const ChainArgs &a) {
     a.vel[i] = f4(v);
     a.J[i] = f4(J);
     a.lam[i] = s_lam[i];
-    if (a.md_accum)  // spread (3): the bead's 8 corner shares into the sums
+    if (a.md_accum == kSumGlobal)  // spread (3): the bead's 8 corner shares into the sums
 #pragma unroll
       for (int k = 0; k < 8; ++k) spread_add(a, 8 * i + k, f4(J));
   }
+  if (a.md_accum == kSumShared) spread_sum_shared(a, smem4, bead, i, J);
   // Translocation bookkeeping (Sec. III): unwrapped x = origin + hi + lo
   const float xrel = bead ? ((float)(a.ox - a.wall_x) + rh.x) + rl.x : 0.f;
   const bool finite = isfinite(rh.x) && isfinite(rh.y) && isfinite(rh.z) && isfinite(v.x) &&
                       isfinite(v.y) && isfinite(v.z);
   const int nt = __syncthreads_count(bead && a.has_wall && xrel < 0.f);
   // every share of this chain is summed (barrier above): the owners' records
-  if (a.md_accum && bead)
+  if (a.md_accum == kSumGlobal && bead)
 #pragma unroll
     for (int k = 0; k < 8; ++k) spread_finalize(a, 8 * i + k);
   const int nan = __syncthreads_or(bead && !finite);
@@ -919,7 +1000,7 @@ __device__ F3 gather_pair(const ChainArgs &a, const void *f, int e, bool valid) 
     a.sp_node[e] = node;
     a.sp_w[e] = wn;
     if (node >= 0) {
-      atomicMin(a.owner + node, e);  // the node's spread owner: its smallest entry
+      if (a.owner != nullptr) atomicMin(a.owner + node, e);  // the node's spread owner: its smallest entry
       const int x = node % g.nx, yz = node / g.nx;
       const int y = yz % g.ny, z = yz / g.ny;
       float h[kQ];

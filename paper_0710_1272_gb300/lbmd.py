@@ -17,6 +17,7 @@ from . import build as _build
 
 LBMD_OK, LBMD_EINVAL, LBMD_ESIZE, LBMD_ECUDA, LBMD_EUNSUPPORTED = 0, -1, -2, -3, -4
 RUNNING, TRANSLOCATED, RETRACTED, NAN, SHAKE_FAIL = range(5)
+ENS_XPAIR = 3  # ensemble tuning: two x-adjacent nodes per thread (16-bit storage)
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 FORCING = {"paper": 0, "guo": 1}
 COUPLING = {"trilinear": 0, "ngp": 1}

@@ -181,7 +181,7 @@ def test_ensemble_autotune_leaves_the_state_unchanged():
     assert ms > 0
     t = a.tuning()
     assert t["rows"] in (4, 8, 16) and t["warps"] in (32, 48) and 1 <= t["claim"] <= 8
-    assert t["cells_per_thread"] in (1, 2)
+    assert t["cells_per_thread"] in (1, 2, lb.ENS_XPAIR)
     a.step(6)
     b.step(11)
     for k in range(len(members)):
@@ -203,6 +203,50 @@ def test_ensemble_tile_shapes_agree(rows, warps, claim, cpt):
     b.step(7)
     for k in range(len(members)):
         assert np.array_equal(a.populations(k), b.populations(k)), k
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("rows,claim", [(4, 2), (8, 5)])
+def test_ensemble_xpair_tiles_agree(storage, rows, claim):
+    """16-bit storage with two x-adjacent nodes per thread (tiles of 64 x rows
+    nodes, pairs of one 32-bit word): the same bits as one node per thread,
+    with a chain and without."""
+    lb = _lb()
+    members, starts = ragged_members(storage)
+    a = lb.Ensemble(members, starts)
+    b = lb.Ensemble(members, starts)
+    a.set_tuning(rows, 32, claim, lb.ENS_XPAIR)
+    assert a.tuning()["cells_per_thread"] == lb.ENS_XPAIR
+    a.step(9)
+    b.step(9)
+    for k in range(len(members)):
+        assert np.array_equal(a.populations(k), b.populations(k)), k
+        assert np.array_equal(a.beads(k)[0], b.beads(k)[0]), k
+
+
+def test_ensemble_xpair_needs_16_bit_storage():
+    lb = _lb()
+    members, starts = ragged_members("f32")
+    ens = lb.Ensemble(members, starts)
+    with pytest.raises(lb.LbmdError):
+        ens.set_tuning(8, 32, 2, lb.ENS_XPAIR)
+
+
+def test_ensemble_long_chain_global_sum_matches_single_box():
+    """A chain longer than the MD block's shared spread table (600 beads)
+    sums its spread with global atomics in the ensemble's MD epilogue and
+    with two kernels in the single box; both give the same bits, beside a
+    short chain summed in shared memory."""
+    lb = _lb()
+    members = [si.ragged_member(600, 5, seed=61, lj_eps=PAPER_EPS),
+               si.ragged_member(20, 3, seed=62, lj_eps=PAPER_EPS)]
+    starts = [si.saw_chain(m, m["seed"]) for m in members]
+    ens = lb.Ensemble(members, starts)
+    ens.step(6)
+    for k, (m, pos) in enumerate(zip(members, starts)):
+        sim = lb.Simulation(m, init_pos=pos)
+        advance_like_member(sim, 6, lb.RUNNING)
+        same_state(ens, k, sim)
 
 
 def test_ensemble_kernel_timing():
