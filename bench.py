@@ -385,7 +385,12 @@ def run_ours(args):
     bytes_per_launch = BYTES_PER_NODE[args.storage] * fluid
     lb_avg_s = lb_ms / 1e3 / max(lb_n, 1)
     achieved = bytes_per_launch / lb_avg_s / 1e9
-    kernel = "k_aa_stream_collide" if args.streaming == "aa" else "k_stream_collide"
+    if args.streaming == "aa":
+        kernel = "k_aa_stream_collide"
+    elif args.storage != "f32" and p["nx"] % 2 == 0:
+        kernel = "k_stream_collide_pair"  # 16-bit storage, two x-adjacent nodes per thread
+    else:
+        kernel = "k_stream_collide"
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "lb_stream_collide_traffic.json")
     if os.path.exists(tpath):
@@ -576,6 +581,8 @@ def ensemble_leg(args, lb, torch, dist, rank, world):
 KERNEL_SOURCES = {
     "k_stream_collide": ("lb_kernels.cu", "lb_collide.cuh", "lb_pull.cuh", "lbmd_common.cuh",
                          "lbmd_internal.h"),
+    "k_stream_collide_pair": ("lb_kernels.cu", "lb_collide.cuh", "lb_pull.cuh", "lbmd_common.cuh",
+                              "lbmd_internal.h"),
     "k_aa_stream_collide": ("lb_aa.cu", "lb_aa.cuh", "lb_collide.cuh", "lb_pull.cuh",
                             "lbmd_common.cuh", "lbmd_internal.h"),
 }

@@ -31,10 +31,10 @@ def test_launches_per_step():
 def test_traffic_records_name_the_bench_workload():
     with open(os.path.join(ROOT, "profiles", "lb_stream_collide_traffic.json")) as f:
         records = json.load(f)["records"]
-    name = bench.workload_name(bench.workload(0, "f32", _Args()))
     for r in records:
         assert r["kernel"] in bench.KERNEL_SOURCES
-        assert r["workload"] == name and r["storage"] == "f32"
+        assert r["storage"] in ("f32", "f16", "bf16")
+        assert r["workload"] == bench.workload_name(bench.workload(0, r["storage"], _Args()))
         assert len(r["kernel_rev"]) == 16 and r["bytes_per_launch"] > 0
         assert os.path.exists(os.path.join(ROOT, r["source"]))
 
