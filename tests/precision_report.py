@@ -15,7 +15,9 @@ costs, next to the FP32 path, and prints a markdown report:
     so this uses the small boxes of the ragged ensemble.
  3. The time-versus-length exponent alpha (mean t ~ N^alpha) at eps = 2e-3
     over N in {50, 100, 200, 400}, 32 seeds per N, from GPU ensembles per
-    storage; and over N in {20, 50, 100} on 4 seeds shared with the oracle.
+    storage, and against the FP64 oracle's runs of the same seeds
+    (tests/golden/oracle_transloc_eps2e-3.txt): per-N means within the
+    oracle's 95 % interval, per-seed differences and the exponents.
  4. The same exponent with and without the solvent (Sec. III compares the
     two), and the cost of a step with and without it at constant volume.
  5. The chain diagnostics of Sec. III over ensembles at two friction values:
@@ -23,12 +25,15 @@ costs, next to the FP32 path, and prints a markdown report:
     the fluid's work rate, the mean work rates and the kinetic energy.
 
   python tests/precision_report.py [section ...]   # needs a CUDA device; default: all
+  ALPHA_DUMP=runs.json python tests/precision_report.py 3   # also saves the GPU runs
+  python tests/precision_report.py alpha-from runs.json      # section 3 again, no GPU
 
 The oracle ensembles run in a spawn-started process pool (one realisation
 per worker, one thread each) created before the first GPU call.
 """
 from __future__ import annotations
 
+import json
 import multiprocessing as mp
 import os
 import sys
@@ -125,57 +130,110 @@ def section_transloc(lb, pool):
     print()
 
 
-def section_alpha(lb, pool):
-    print("## 3. Exponent alpha of mean t ~ N^alpha, eps = 2e-3, 5x5 pore\n")
-    ns = (50, 100, 200, 400)
-    members, starts, which = [], [], []
-    for n in ns:
-        for s in range(32):
+ALPHA_NS = (50, 100, 200, 400)
+ALPHA_SEEDS = 32
+ORACLE_FILE = os.path.join(ROOT, "tests", "golden", "oracle_transloc_eps2e-3.txt")
+
+
+def alpha_members():
+    """The realisations of the exponent runs: ragged-ensemble boxes, 5x5 pore,
+    eps = 2e-3, seeds 3000 + 1000 N + s (the seeds of the oracle runs in
+    tests/golden/oracle_transloc_eps2e-3.txt)."""
+    members, starts, which, seeds = [], [], [], []
+    for n in ALPHA_NS:
+        for s in range(ALPHA_SEEDS):
             p = si.ragged_member(n, 5, seed=3000 + 1000 * n + s, lj_eps=2e-3)
             members.append(p)
             starts.append(si.saw_chain(p, p["seed"]))
             which.append(n)
-    which = np.array(which)
-    print("| storage | " + " | ".join(f"mean t (N={n})" for n in ns) + " | alpha | translocated | wall s |")
-    print("|---|" + "---|" * len(ns) + "---|---|---|")
+            seeds.append(s)
+    return members, starts, np.array(which), np.array(seeds)
+
+
+def alpha_gpu_runs(lb):
+    """GPU ensembles of the exponent runs per storage: {storage: [(N, s, state,
+    t_transloc), ...], "wall_s": {...}}."""
+    members, starts, which, seeds = alpha_members()
+    out = {"wall_s": {}}
     for st in STORAGES:
         ens = lb.Ensemble([dict(m, storage=st) for m in members], starts)
         ens.autotune(2)
         t0 = time.perf_counter()
         ens.run(150000, check_every=2048)
-        wall = time.perf_counter() - t0
+        out["wall_s"][st] = time.perf_counter() - t0
         r = ens.results()
         del ens
-        ok = r["state"] == lb.TRANSLOCATED
-        means = [r["t_transloc"][(which == n) & ok].mean() for n in ns]
-        print(f"| {st} | " + " | ".join(f"{m:.0f}" for m in means) +
-              f" | {alpha_fit(ns, means):.3f} | {ok.sum()}/{len(members)} | {wall:.0f} |")
-    print()
-    # shared seeds with the oracle on the small boxes
-    ns2 = (20, 50, 100)
-    members, starts, which = [], [], []
-    for n in ns2:
-        for s in range(4):
-            p = si.ragged_member(n, 5, seed=4000 + 1000 * n + s, lj_eps=2e-3)
-            members.append(p)
-            starts.append(si.saw_chain(p, p["seed"]))
-            which.append(n)
-    which = np.array(which)
-    t_o = np.array(pool.map(_oracle_run, [(p, pos, 20000) for p, pos in zip(members, starts)]))
-    mo = [t_o[which == n].mean() for n in ns2]
-    print("| N in {20, 50, 100}, 4 shared seeds | " + " | ".join(f"mean t (N={n})" for n in ns2)
-          + " | alpha | max per-seed |t_GPU - t_oracle| |")
-    print("|---|" + "---|" * len(ns2) + "---|---|")
-    print("| oracle | " + " | ".join(f"{m:.1f}" for m in mo) + f" | {alpha_fit(ns2, mo):.4f} | - |")
+        out[st] = [(int(n), int(k), int(a), int(b)) for n, k, a, b in
+                   zip(which, seeds, r["state"], r["t_transloc"])]
+    return out
+
+
+def oracle_runs():
+    """{(N, s): (state, t_transloc)} from the committed oracle file."""
+    got = {}
+    if os.path.exists(ORACLE_FILE):
+        for line in open(ORACLE_FILE):
+            if line.strip() and not line.startswith("#"):
+                f = line.split()
+                got[(int(f[0]), int(f[1]))] = (int(f[3]), int(f[4]))
+    return got
+
+
+def print_alpha(gpu):
+    print("## 3. Exponent alpha of mean t ~ N^alpha, eps = 2e-3, 5x5 pore\n")
+    print(f"GPU: {ALPHA_SEEDS} seeds per N (s = 0 .. {ALPHA_SEEDS - 1}), one ragged ensemble per storage. "
+          "Oracle: the FP64 runs of `tests/golden/oracle_transloc_eps2e-3.txt` (written by "
+          "`tests/golden/make_oracle_transloc.py`, one realisation per host core), same seeds and starts.\n")
+    print("| storage | " + " | ".join(f"mean t (N={n})" for n in ALPHA_NS) + " | alpha | translocated | wall s |")
+    print("|---|" + "---|" * len(ALPHA_NS) + "---|---|---|")
     for st in STORAGES:
-        ens = lb.Ensemble([dict(m, storage=st) for m in members], starts)
-        ens.run(20000, check_every=512)
-        r = ens.results()
-        del ens
-        mg = [r["t_transloc"][which == n].mean() for n in ns2]
-        print(f"| {st} | " + " | ".join(f"{m:.1f}" for m in mg) + f" | {alpha_fit(ns2, mg):.4f} | "
-              f"{np.abs(r['t_transloc'] - t_o).max()} |")
+        rows = gpu[st]
+        means = [np.mean([t for n2, _, a, t in rows if n2 == n and a == 1]) for n in ALPHA_NS]
+        ok = sum(1 for r in rows if r[2] == 1)
+        print(f"| {st} | " + " | ".join(f"{m:.0f}" for m in means) +
+              f" | {alpha_fit(ALPHA_NS, means):.3f} | {ok}/{len(rows)} | {gpu['wall_s'][st]:.0f} |")
     print()
+    orc = oracle_runs()
+    ns = [n for n in ALPHA_NS if any(k[0] == n for k in orc)]
+    if not ns:
+        print("(no oracle runs yet)\n")
+        return
+    print("Against the oracle on the seeds it has run (t of translocated realisations; "
+          "95 % interval of the oracle mean; per-seed difference |t_GPU - t_oracle|):\n")
+    print("| N | oracle seeds | oracle mean +- 95% | storage | GPU mean, same seeds | |GPU - oracle| / half-width | max per-seed diff | median per-seed diff |")
+    print("|---|---|---|---|---|---|---|---|")
+    alpha_rows = {}
+    for n in ns:
+        sd = sorted(k[1] for k in orc if k[0] == n and orc[k][0] == 1)
+        to = np.array([orc[(n, k)][1] for k in sd], dtype=float)
+        if to.size < 2:
+            continue
+        mo, ho = ci95(to)
+        alpha_rows.setdefault("oracle", []).append((n, mo))
+        for st in STORAGES:
+            gmap = {k: (a, t) for n2, k, a, t in gpu[st] if n2 == n}
+            tg = np.array([gmap[k][1] if gmap[k][0] == 1 else np.nan for k in sd], dtype=float)
+            mg = np.nanmean(tg)
+            alpha_rows.setdefault(st, []).append((n, mg))
+            d = np.abs(tg - to)
+            print(f"| {n} | {to.size} | {mo:.1f} +- {ho:.1f} | {st} | {mg:.1f} | {abs(mg - mo) / ho:.2f} | "
+                  f"{np.nanmax(d):.0f} | {np.nanmedian(d):.0f} |")
+    print()
+    if len(alpha_rows.get("oracle", [])) >= 2:
+        ao = alpha_fit([n for n, _ in alpha_rows["oracle"]], [m for _, m in alpha_rows["oracle"]])
+        print(f"Exponent over N in {{{', '.join(str(n) for n, _ in alpha_rows['oracle'])}}} on the oracle's seeds: "
+              f"oracle {ao:.4f}; " + "; ".join(
+                  f"{st} {alpha_fit([n for n, _ in alpha_rows[st]], [m for _, m in alpha_rows[st]]):.4f} "
+                  f"(|diff| {abs(alpha_fit([n for n, _ in alpha_rows[st]], [m for _, m in alpha_rows[st]]) - ao):.4f})"
+                  for st in STORAGES) + ".\n")
+
+
+def section_alpha(lb, pool, dump=None):
+    gpu = alpha_gpu_runs(lb)
+    if dump:
+        with open(dump, "w") as f:
+            json.dump({k: v for k, v in gpu.items()}, f)
+    print_alpha(gpu)
 
 
 def section_solvent(lb):
@@ -267,6 +325,11 @@ def section_diagnostics(lb):
 
 
 def main():
+    if len(sys.argv) > 2 and sys.argv[1] == "alpha-from":
+        # section 3 from saved GPU runs and the oracle file (no GPU needed)
+        with open(sys.argv[2]) as f:
+            print_alpha(json.load(f))
+        return 0
     ctx = mp.get_context("spawn")
     with ctx.Pool(processes=max(1, os.cpu_count() or 1)) as pool:
         import oracle
@@ -287,7 +350,7 @@ def main():
         if "2" in want:
             section_transloc(lb, pool)
         if "3" in want:
-            section_alpha(lb, pool)
+            section_alpha(lb, pool, os.environ.get("ALPHA_DUMP"))
         if "4" in want:
             section_solvent(lb)
         if "5" in want:
