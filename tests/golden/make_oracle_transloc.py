@@ -10,11 +10,11 @@ precision report use, so the two sides run the same starts.  Each realisation
 runs until it leaves the running state or reaches CAP steps.
 
 One realisation per worker process (one OpenMP thread each), longest chains
-first.  Every finished realisation is appended as one line at once, so an
+first unless the lengths are given (then in the order given).  Every finished realisation is appended as one line at once, so an
 interrupted run keeps what it finished and a re-run skips those.  Only the
 oracle and the seeded input generators are called.
 
-  python tests/golden/make_oracle_transloc.py [workers]
+  python tests/golden/make_oracle_transloc.py [workers] [N ...]   # default: all lengths
 """
 from __future__ import annotations
 
@@ -69,8 +69,9 @@ def done_jobs():
 
 def main():
     workers = int(sys.argv[1]) if len(sys.argv) > 1 else (os.cpu_count() or 1)
+    lengths = tuple(int(a) for a in sys.argv[2:]) or LENGTHS
     have = done_jobs()
-    jobs = [(n, s) for n in LENGTHS for s in range(SEEDS) if (n, s) not in have]
+    jobs = [(n, s) for n in lengths for s in range(SEEDS) if (n, s) not in have]
     if not os.path.exists(OUT):
         with open(OUT, "w") as f:
             f.write("# FP64 oracle translocation runs, eps = 2e-3, 5x5 pore, ragged-ensemble boxes\n")
