@@ -103,12 +103,17 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     if (t[3] && (e = record_timing(t[3], c->own)) != cudaSuccess) return e;
     for (int k : {0, 1, 4})
       if (t[k] && (e = record_timing(t[k], c->own)) != cudaSuccess) return e;
-    if ((e = launch_spread_apply(c->p.storage, c->geo, c->chain, B, mode_out, c->status, c->own)) !=
-        cudaSuccess)
+    if ((e = launch_spread_apply(c->p.storage, c->geo, c->chain, B, mode_out, false, c->status,
+                                 c->own)) != cudaSuccess)
       return e;
     if (t[5] && (e = record_timing(t[5], c->own)) != cudaSuccess) return e;
     return cudaSuccess;
   }
+  // With 16-bit storage the MD path sets the step (its stream-collide is the
+  // shorter branch): the apply converts the owners' sums itself, one launch
+  // fewer on that path.  With FP32 the stream-collide sets it, and the
+  // conversion runs beside it, keeping the apply after it short.
+  const bool take = c->p.storage != LBMD_STORE_F32;
   if (c->N > 0) {
     // (1) gather from the pre-step populations, then fork: the MD cycle runs
     // on the side stream while the stream-collide runs on the main one
@@ -122,7 +127,7 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     if ((e = launch_md_cycle(a, c->prio_high, c->side)) != cudaSuccess) return e;
     if (t[3] && (e = record_timing(t[3], c->side)) != cudaSuccess) return e;
     // sum part of the spread, beside the stream-collide
-    if ((e = launch_spread_sum(c->chain, c->side)) != cudaSuccess) return e;
+    if ((e = launch_spread_sum(c->chain, !take, c->side)) != cudaSuccess) return e;
   } else if (t[2]) {
     if ((e = record_timing(t[2], c->own)) != cudaSuccess) return e;
     if ((e = record_timing(t[3], c->own)) != cudaSuccess) return e;
@@ -146,8 +151,8 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     if ((e = cudaEventRecord(c->ev_join, c->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(c->own, c->ev_join, 0)) != cudaSuccess) return e;
     if (t[4] && (e = record_timing(t[4], c->own)) != cudaSuccess) return e;
-    if ((e = launch_spread_apply(c->p.storage, c->geo, c->chain, B, mode_out, c->status, c->own)) !=
-        cudaSuccess)
+    if ((e = launch_spread_apply(c->p.storage, c->geo, c->chain, B, mode_out, take, c->status,
+                                 c->own)) != cudaSuccess)
       return e;
     if (t[5] && (e = record_timing(t[5], c->own)) != cudaSuccess) return e;
   } else if (t[4]) {

@@ -219,7 +219,8 @@ cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s);
 //  - apply (after the stream-collide): each owner entry adds the source
 //    S_p = 3 w_p c_p . F to its node's post-collision populations of `dst` in
 //    layout `mode` -- the only write to those words.
-// launch_spread_sum enqueues the sum as two kernels (chains whose MD block
+// launch_spread_sum enqueues the sum as two kernels, or only the first when
+// the apply converts the sums itself (records == false; chains whose MD block
 // sums instead have md_accum set).
 // A single box sums with the owner field and global atomics in two kernels
 // after the MD cycle (kSumKernels: spread over many SMs, whose global memory
@@ -233,10 +234,12 @@ cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s);
 constexpr int kOwnerFree = 0x7f7f7f7f;
 constexpr int kSumKernels = 0, kSumGlobal = 1, kSumShared = 2;
 constexpr int kSumSharedMaxN = 512;
-cudaError_t launch_spread_sum(const ChainArgs &a, cudaStream_t s);
-// `bump` (may be null): status->step += 1 by one thread.
+cudaError_t launch_spread_sum(const ChainArgs &a, bool records, cudaStream_t s);
+// `take`: the owners' forces from their fixed-point sums (the sum ran with
+// records == false), else from the records.  `bump` (may be null):
+// status->step += 1 by one thread.
 cudaError_t launch_spread_apply(int storage, const LbGeom &g, const ChainArgs &a, void *dst,
-                                int mode, DevStatus *bump, cudaStream_t s);
+                                int mode, bool take, DevStatus *bump, cudaStream_t s);
 // Ensemble launchers.  `live` points at the flags of the current step (one int
 // per realisation); realisations whose flag is 0 are skipped by every kernel.
 // Stream-collide: persistent grid of `grid` blocks of 32 x rows threads (rows

@@ -1111,11 +1111,14 @@ __global__ void __launch_bounds__(256) k_spread_finalize(ChainArgs a) {
 // step), or [p][x_k + c_p] -- [opp(p)][x_k] if x_k + c_p is solid -- (in
 // place, after an odd step).  No other thread writes those words in this
 // kernel: FP32 adds with one atomic each (no read-back); 16-bit storage reads
-// the 18 words first and writes each rounded once.
-template <int S>
+// the 18 words first and writes each rounded once.  The owner's force comes
+// from its record sp_src[e] (TAKE = false: converted by k_spread_finalize) or
+// straight from its fixed-point sum (TAKE = true: the conversion of
+// spread_finalize done here, one launch fewer after the MD cycle).
+template <int S, bool TAKE>
 __global__ void __launch_bounds__(256)
-    k_spread_apply(LbGeom g, const float4 *__restrict__ src, int nw, typename Store<S>::T *dst,
-                   int mode, DevStatus *bump) {
+    k_spread_apply(LbGeom g, ChainArgs a, int nw, typename Store<S>::T *dst, int mode,
+                   DevStatus *bump) {
   using St = Store<S>;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (bump != nullptr && e == 0) {
@@ -1124,10 +1127,18 @@ __global__ void __launch_bounds__(256)
     if (bump->pop_bad && bump->state == LBMD_RUNNING) bump->state = LBMD_NAN;
   }
   if (e >= nw) return;
-  const float4 v = src[e];
-  const int node = __float_as_int(v.w);
-  if (node < 0) return;  // not an owner
-  const F3 F{v.x, v.y, v.z};
+  int node;
+  F3 F;
+  if (TAKE) {
+    node = a.sp_node[e];
+    if (node < 0 || a.owner[node] != e) return;  // not an owner
+    F = spread_take(a, node, e);
+  } else {
+    const float4 v = a.sp_src[e];
+    node = __float_as_int(v.w);
+    if (node < 0) return;  // not an owner
+    F = F3{v.x, v.y, v.z};
+  }
   const size_t Vp = (size_t)g.Vp;
   uint32_t bb = 0u;
   int x = 0, y = 0, z = 0;
@@ -1164,31 +1175,34 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-cudaError_t launch_spread_sum(const ChainArgs &a, cudaStream_t s) {
+cudaError_t launch_spread_sum(const ChainArgs &a, bool records, cudaStream_t s) {
   if (a.N <= 0) return cudaSuccess;
   const int blocks = (8 * a.N + 255) / 256;
   k_spread_accum<<<blocks, 256, 0, s>>>(a);
-  k_spread_finalize<<<blocks, 256, 0, s>>>(a);
+  if (records) k_spread_finalize<<<blocks, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
+template <int S>
+static void apply_as(bool take, int blocks, const LbGeom &g, const ChainArgs &a, int nw, void *dst,
+                     int mode, DevStatus *bump, cudaStream_t s) {
+  using T = typename Store<S>::T;
+  if (take)
+    k_spread_apply<S, true><<<blocks, 256, 0, s>>>(g, a, nw, (T *)dst, mode, bump);
+  else
+    k_spread_apply<S, false><<<blocks, 256, 0, s>>>(g, a, nw, (T *)dst, mode, bump);
+}
+
 cudaError_t launch_spread_apply(int storage, const LbGeom &g, const ChainArgs &a, void *dst,
-                                int mode, DevStatus *bump, cudaStream_t s) {
-  const int nw = a.sp_src ? 8 * a.N : 0;  // no records without a coupled chain
+                                int mode, bool take, DevStatus *bump, cudaStream_t s) {
+  // no records and no sums without a coupled chain
+  const int nw = (take ? a.owner != nullptr : a.sp_src != nullptr) ? 8 * a.N : 0;
   const int blocks = nw > 0 ? (nw + 255) / 256 : 1;
   switch (storage) {
-    case LBMD_STORE_F32:
-      k_spread_apply<LBMD_STORE_F32><<<blocks, 256, 0, s>>>(g, a.sp_src, nw, (float *)dst, mode, bump);
-      break;
-    case LBMD_STORE_F16:
-      k_spread_apply<LBMD_STORE_F16><<<blocks, 256, 0, s>>>(g, a.sp_src, nw, (__half *)dst, mode, bump);
-      break;
-    case LBMD_STORE_BF16:
-      k_spread_apply<LBMD_STORE_BF16><<<blocks, 256, 0, s>>>(g, a.sp_src, nw, (__nv_bfloat16 *)dst, mode,
-                                                             bump);
-      break;
-    default:
-      return cudaErrorInvalidValue;
+    case LBMD_STORE_F32: apply_as<LBMD_STORE_F32>(take, blocks, g, a, nw, dst, mode, bump, s); break;
+    case LBMD_STORE_F16: apply_as<LBMD_STORE_F16>(take, blocks, g, a, nw, dst, mode, bump, s); break;
+    case LBMD_STORE_BF16: apply_as<LBMD_STORE_BF16>(take, blocks, g, a, nw, dst, mode, bump, s); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

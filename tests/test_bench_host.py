@@ -19,8 +19,9 @@ def test_launches_per_step():
     p = bench.workload(0, "f32", _Args())
     # gather, MD cycle, stream-collide, spread sum (two kernels) and apply
     assert bench.launches_per_step(p) == 6
-    p = bench.workload(0, "f16", _Args())
-    assert bench.launches_per_step(p) == 6
+    # 16-bit storage: the apply converts the sums (one sum kernel)
+    for st in ("f16", "bf16"):
+        assert bench.launches_per_step(bench.workload(0, st, _Args())) == 5
     a = _Args()
     a.workload = "solvent"
     assert bench.launches_per_step(bench.workload(0, "f32", a)) == 1
