@@ -351,7 +351,7 @@ int lbmd_destroy(lbmd_ctx *ctx);
  * storage type and forcing -- through one set of launches per LB step: the
  * gather and the spread over every bead of every realisation, one MD block
  * per chain (chains grouped by block size, the groups run concurrently) and
- * one persistent stream-collide kernel over a shared list of tiles (32 x rows
+ * one stream-collide kernel over a shared list of tiles (32 x rows
  * consecutive nodes of one z-plane) of every live realisation.  Steps are replayed from
  * CUDA graphs of 1, 2 and 16 steps.
  *
@@ -427,8 +427,9 @@ int lbmd_ensemble_read_diagnostics(lbmd_ensemble *ens, int32_t member, lbmd_diag
 /*
  * Launch shape of the ensemble stream-collide: tile height rows (4, 8 or 16
  * rows of 32 consecutive nodes), register budget for warps resident warps per
- * SM (32: 64 registers, or 48: 40 registers), tiles taken per claim of the
- * work counter (1 .. 64) and cells per thread: 1; 2, the nodes at the same
+ * SM (32: 64 registers, or 48: 40 registers), tiles per block `claim`
+ * (1 .. 64; one block per claim tiles of the live realisations) and cells
+ * per thread: 1; 2, the nodes at the same
  * (x, y) on two consecutive z-planes; or LBMD_ENS_XPAIR, two x-adjacent
  * nodes whose 16-bit deviations share one 32-bit word (16-bit storage only;
  * tiles of 64 x rows nodes).  The two-cell shapes need warps = 32 and rows 4

@@ -2,7 +2,7 @@
 // independent translocation realisations (Sec. III, ensembles over initial
 // chains) stepped together.  Every realisation keeps the workspace layout of a
 // single box; the ensemble adds the descriptor array, the tile list of the
-// persistent stream-collide, the (realisation, bead) table of the gather and
+// stream-collide, the (realisation, bead) table of the gather and
 // spread, the chain lists of the MD groups and the live flags.
 #include <cuda_runtime.h>
 
@@ -25,7 +25,7 @@ constexpr int kEnsBlock = 16;   // steps per long graph
 const int kEnsGraphSteps[3] = {1, 2, kEnsBlock};
 
 struct EnsLayout {
-  size_t mem, lbd, tiles, n_tiles, counter, beads, live, cap, chains, stage;
+  size_t mem, lbd, tiles, n_tiles, beads, live, cap, chains, stage;
   size_t stage_floats;
   size_t max_tiles;  // tile capacity (rows = 4, every realisation)
   int nb;            // padded bead slots
@@ -88,7 +88,6 @@ EnsLayout make_ens_layout(const lbmd_params *m, int32_t count) {
   E.lbd = take((size_t)count * sizeof(EnsLb));
   E.tiles = take(std::max<size_t>(E.max_tiles, 1) * sizeof(EnsTile));
   E.n_tiles = take(sizeof(int));
-  E.counter = take(sizeof(int));
   E.beads = take((size_t)std::max(E.nb, 1) * sizeof(int2));
   E.live = take(2 * (size_t)count * sizeof(int));
   E.cap = take(sizeof(long long));
@@ -122,7 +121,7 @@ struct lbmd_ensemble {
   EnsMember *d_mem;
   EnsLb *d_lbd;
   EnsTile *d_tiles;
-  int *d_n_tiles, *d_counter, *d_live, *d_chains;
+  int *d_n_tiles, *d_live, *d_chains;
   int2 *d_beads;
   long long *d_cap;
   float *stage;
@@ -205,7 +204,14 @@ cudaError_t upload_tiles(lbmd_ensemble *e, const std::vector<int> &live) {
   if ((err = cudaMemcpyAsync(e->d_n_tiles, &n, sizeof(int), cudaMemcpyHostToDevice, e->own)) != cudaSuccess)
     return err;
   e->tiles_live = n_live;
-  return cudaStreamSynchronize(e->own);
+  if ((err = cudaStreamSynchronize(e->own)) != cudaSuccess) return err;
+  // one stream-collide block per `claim` tiles; the graphs hold the grid size
+  const int grid = std::max(1, (n + e->claim - 1) / e->claim);
+  if (grid != e->grid) {
+    drop_graphs(e);
+    e->grid = grid;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t read_live(lbmd_ensemble *e, std::vector<int> &live) {
@@ -274,7 +280,7 @@ cudaError_t enqueue_ens_step(lbmd_ensemble *e, int cur) {
   int *live_next = e->d_live + (cur ^ 1) * e->count;
   if (t[0] && (err = cudaEventRecord(t[0], e->own)) != cudaSuccess) return err;
   if (!e->solvent_free &&
-      (err = launch_ens_gather(e->storage, e->d_mem, e->d_beads, e->E.nb, live, cur, e->d_counter,
+      (err = launch_ens_gather(e->storage, e->d_mem, e->d_beads, e->E.nb, live, cur,
                                e->own)) != cudaSuccess)
     return err;
   if ((err = cudaEventRecord(e->ev_fork, e->own)) != cudaSuccess) return err;
@@ -289,7 +295,7 @@ cudaError_t enqueue_ens_step(lbmd_ensemble *e, int cur) {
   if (t[1] && (err = cudaEventRecord(t[1], e->own)) != cudaSuccess) return err;
   if (!e->solvent_free &&
       (err = launch_ens_stream_collide(e->storage, e->forcing, e->rows, e->warps, e->cpt, e->claim, e->grid,
-                                       e->d_lbd, e->d_tiles, e->d_n_tiles, e->d_counter, live, cur,
+                                       e->d_lbd, e->d_tiles, e->d_n_tiles, live, cur,
                                        e->own)) != cudaSuccess)
     return err;
   if (t[2] && (err = cudaEventRecord(t[2], e->own)) != cudaSuccess) return err;
@@ -348,10 +354,14 @@ int enqueue_steps(lbmd_ensemble *e, int64_t n) {
   return LBMD_OK;
 }
 
+// One stream-collide block per `claim` tiles of the current tile list.  A
+// new grid size drops the captured graphs (they hold the old one).
 int set_grid(lbmd_ensemble *e) {
   const int per_sm = ens_lb_blocks_per_sm(e->storage, e->forcing, e->rows, e->warps, e->cpt);
   if (per_sm < 1) return fail(LBMD_EINVAL, "no ensemble stream-collide of this launch shape");
-  e->grid = e->sms * per_sm;
+  const int grid = std::max(1, (int)((e->htiles.size() + e->claim - 1) / e->claim));
+  if (grid != e->grid) drop_graphs(e);
+  e->grid = grid;
   return LBMD_OK;
 }
 
@@ -430,7 +440,6 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
   e->d_lbd = (EnsLb *)(e->ws + E.lbd);
   e->d_tiles = (EnsTile *)(e->ws + E.tiles);
   e->d_n_tiles = (int *)(e->ws + E.n_tiles);
-  e->d_counter = (int *)(e->ws + E.counter);
   e->d_beads = (int2 *)(e->ws + E.beads);
   e->d_live = (int *)(e->ws + E.live);
   e->d_cap = (long long *)(e->ws + E.cap);
@@ -527,7 +536,6 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
   e->nside = std::min<int>(kEnsSide, std::max<int>(1, (int)e->groups.size()));
   std::vector<int> live0(2 * (size_t)count, 0);
   std::fill(live0.begin(), live0.begin() + count, 1);
-  const int zero = 0;
   cudaStream_t s = e->user;
   if ((err = cudaMemcpyAsync(e->d_mem, e->hmem.data(), count * sizeof(EnsMember), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(err, "upload");
   if ((err = cudaMemcpyAsync(e->d_lbd, e->hlbd.data(), count * sizeof(EnsLb), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(err, "upload");
@@ -535,7 +543,6 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
   if ((err = cudaMemcpyAsync(e->d_chains, chains.data(), chains.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(err, "upload");
   if ((err = cudaMemcpyAsync(e->d_live, live0.data(), live0.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(err, "upload");
   if ((err = cudaMemcpyAsync(e->d_cap, &e->cap, sizeof(long long), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(err, "upload");
-  if ((err = cudaMemcpyAsync(e->d_counter, &zero, sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) return bail(err, "upload");
   if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return bail(err, "create sync");
   if ((rc = set_grid(e))) {
     destroy_ens(e);
@@ -759,21 +766,19 @@ int lbmd_ensemble_autotune(lbmd_ensemble *e, int32_t trials, double *best_ms) {
       const int per_sm = ens_lb_blocks_per_sm(e->storage, e->forcing, rows, warps, cpt);
       if (per_sm < 1) continue;
       for (int claim : {1, 2, 4, 8}) {
-        // one untimed launch, then `trials` timed ones; the counter is reset
-        // before each launch as the gather does in a step
+        // one untimed launch, then `trials` timed ones
+        const int grid = std::max(1, (int)((e->htiles.size() + claim - 1) / claim));
         for (int k = 0; k <= trials; ++k) {
-          if ((err = cudaMemsetAsync(e->d_counter, 0, sizeof(int), e->own)) != cudaSuccess) goto done;
           if (k == 1 && (err = cudaEventRecord(t0, e->own)) != cudaSuccess) goto done;
-          if ((err = launch_ens_stream_collide(e->storage, e->forcing, rows, warps, cpt, claim, e->sms * per_sm,
-                                               e->d_lbd, e->d_tiles, e->d_n_tiles, e->d_counter, live,
-                                               cur, e->own)) != cudaSuccess)
+          if ((err = launch_ens_stream_collide(e->storage, e->forcing, rows, warps, cpt, claim, grid,
+                                               e->d_lbd, e->d_tiles, e->d_n_tiles, live, cur,
+                                               e->own)) != cudaSuccess)
             goto done;
         }
         if ((err = cudaEventRecord(t1, e->own)) != cudaSuccess) goto done;
         if ((err = cudaEventSynchronize(t1)) != cudaSuccess) goto done;
         float ms = 0.f;
         if ((err = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess) goto done;
-        // the memsets between launches are included in every shape alike
         const double avg = ms / trials;
         if (avg < best) {
           best = avg;
@@ -796,7 +801,6 @@ done:
   if ((rc = set_grid(e))) return rc;
   drop_graphs(e);
   EK(e, upload_tiles(e, hl));
-  EK(e, cudaMemsetAsync(e->d_counter, 0, sizeof(int), e->own));
   EK(e, cudaEventRecord(e->ev_out, e->own));
   EK(e, cudaStreamWaitEvent(e->user, e->ev_out, 0));
   if (best_ms) *best_ms = best;

@@ -242,11 +242,11 @@ cudaError_t launch_spread_apply(int storage, const LbGeom &g, const ChainArgs &a
                                 int mode, bool take, DevStatus *bump, cudaStream_t s);
 // Ensemble launchers.  `live` points at the flags of the current step (one int
 // per realisation); realisations whose flag is 0 are skipped by every kernel.
-// Stream-collide: persistent grid of `grid` blocks of 32 x rows threads (rows
-// 4, 8 or 16; registers sized for `warps` = 32 or 48 resident warps per SM)
-// taking `claim` tiles at a time from `counter` (reset by the ensemble
-// gather).  Every realisation must have 19 Vp < 2^31 (32-bit offsets) and
-// nx * ny < 2^22 (float row division).
+// Stream-collide: `grid` blocks of 32 x rows threads (rows 4, 8 or 16;
+// registers sized for `warps` = 32 or 48 resident warps per SM), block b
+// updating tiles [b claim, (b + 1) claim) of the *n_tiles listed (blocks past
+// the end return).  Every realisation must have 19 Vp < 2^31 (32-bit offsets)
+// and nx * ny < 2^22 (float row division).
 // forcing: LBMD_FORCING_* or kForcingNone (every realisation has g = 0).
 // cpt: cells per thread, 1; 2 (two consecutive z-planes); or kEnsXPair (two
 // x-adjacent nodes sharing a 32-bit word, 16-bit storage).  The two-cell
@@ -255,13 +255,13 @@ cudaError_t launch_spread_apply(int storage, const LbGeom &g, const ChainArgs &a
 constexpr int kEnsXPair = LBMD_ENS_XPAIR;
 cudaError_t launch_ens_stream_collide(int storage, int forcing, int rows, int warps, int cpt,
                                       int claim, int grid, const EnsLb *lbd, const EnsTile *tiles,
-                                      const int *n_tiles, int *counter, const int *live, int cur,
+                                      const int *n_tiles, const int *live, int cur,
                                       cudaStream_t s);
 // Blocks of that kernel that fit on one SM (0: no such shape).
 int ens_lb_blocks_per_sm(int storage, int forcing, int rows, int warps, int cpt);
 // Gather for every (realisation, bead) of `beads` (padded entries have m < 0).
 cudaError_t launch_ens_gather(int storage, const EnsMember *mem, const int2 *beads, int nb,
-                              const int *live, int cur, int *counter, cudaStream_t s);
+                              const int *live, int cur, cudaStream_t s);
 // MD cycle of the `count` chains listed in `chains`, one block of `threads`
 // threads each, with dynamic shared memory for `max_n` beads.
 cudaError_t launch_ens_md_cycle(const EnsMember *mem, const int *chains, int count, int threads,

@@ -1036,13 +1036,11 @@ __global__ void __launch_bounds__(256) k_gather(ChainArgs a) {
 // Ensemble gather: thread e serves corner e & 7 of padded bead slot e >> 3,
 // beads[slot] = (realisation, bead) or m < 0 for padding.  Every realisation's
 // slots start at a multiple of four, so a warp never mixes realisations.
-// Thread 0 also resets the work counter of this step's stream-collide.
 template <int S>
 __global__ void __launch_bounds__(256)
     k_ens_gather(const EnsMember *__restrict__ mem, const int2 *__restrict__ beads, int nb,
-                 const int *__restrict__ live, int cur, int *counter) {
+                 const int *__restrict__ live, int cur) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e == 0) *counter = 0;
   const int slot = e >> 3;
   int2 mi = make_int2(-1, 0);
   if (slot < nb) mi = beads[slot];
@@ -1259,12 +1257,12 @@ __global__ void __launch_bounds__(256)
 }
 
 cudaError_t launch_ens_gather(int storage, const EnsMember *mem, const int2 *beads, int nb,
-                              const int *live, int cur, int *counter, cudaStream_t s) {
+                              const int *live, int cur, cudaStream_t s) {
   const int blocks = nb > 0 ? (8 * nb + 255) / 256 : 1;
   switch (storage) {
-    case LBMD_STORE_F32: k_ens_gather<LBMD_STORE_F32><<<blocks, 256, 0, s>>>(mem, beads, nb, live, cur, counter); break;
-    case LBMD_STORE_F16: k_ens_gather<LBMD_STORE_F16><<<blocks, 256, 0, s>>>(mem, beads, nb, live, cur, counter); break;
-    case LBMD_STORE_BF16: k_ens_gather<LBMD_STORE_BF16><<<blocks, 256, 0, s>>>(mem, beads, nb, live, cur, counter); break;
+    case LBMD_STORE_F32: k_ens_gather<LBMD_STORE_F32><<<blocks, 256, 0, s>>>(mem, beads, nb, live, cur); break;
+    case LBMD_STORE_F16: k_ens_gather<LBMD_STORE_F16><<<blocks, 256, 0, s>>>(mem, beads, nb, live, cur); break;
+    case LBMD_STORE_BF16: k_ens_gather<LBMD_STORE_BF16><<<blocks, 256, 0, s>>>(mem, beads, nb, live, cur); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
