@@ -101,13 +101,15 @@ def workload(seed: int, storage: str, args=None):
 
 def launches_per_step(p) -> int:
     """Kernels of one coupled step: gather, MD cycle, stream-collide and the
-    spread -- with FP32 storage in three kernels (the fixed-point sum and the
-    owners' records beside the stream-collide, the apply after it), with
-    16-bit storage in two (the apply converts the sums itself); without beads
-    the stream-collide alone, plus the step-count kernel with the thermal
-    source."""
+    spread -- in three kernels when the stream-collide moves 480 MB or more
+    per step (the fixed-point sum and the owners' records beside it, the
+    apply after it), else in two (the apply converts the sums itself); without
+    beads the stream-collide alone, plus the step-count kernel with the
+    thermal source."""
     if p["n_beads"] > 0:
-        return 6 if p.get("storage", "f32") == "f32" else 5
+        nodes = p["nx"] * p["ny"] * p["nz"]
+        bytes_per_step = 2 * 19 * nodes * (4 if p.get("storage", "f32") == "f32" else 2)
+        return 6 if bytes_per_step >= 480_000_000 else 5
     return 2 if p.get("kT_fluid", 0) > 0 else 1
 
 

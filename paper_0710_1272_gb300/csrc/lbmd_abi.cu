@@ -109,11 +109,10 @@ cudaError_t enqueue_step(lbmd_ctx *c, int src) {
     if (t[5] && (e = record_timing(t[5], c->own)) != cudaSuccess) return e;
     return cudaSuccess;
   }
-  // With 16-bit storage the MD path sets the step (its stream-collide is the
-  // shorter branch): the apply converts the owners' sums itself, one launch
-  // fewer on that path.  With FP32 the stream-collide sets it, and the
-  // conversion runs beside it, keeping the apply after it short.
-  const bool take = c->p.storage != LBMD_STORE_F32;
+  // Where the owners' sums are converted: when the MD branch sets the step,
+  // in the apply (one launch fewer on that branch); when the stream-collide
+  // sets it, beside it in k_spread_finalize, keeping the apply after it short.
+  const bool take = spread_take_in_apply(c->p.storage, c->geo.V);
   if (c->N > 0) {
     // (1) gather from the pre-step populations, then fork: the MD cycle runs
     // on the side stream while the stream-collide runs on the main one

@@ -235,6 +235,15 @@ constexpr int kOwnerFree = 0x7f7f7f7f;
 constexpr int kSumKernels = 0, kSumGlobal = 1, kSumShared = 2;
 constexpr int kSumSharedMaxN = 512;
 cudaError_t launch_spread_sum(const ChainArgs &a, bool records, cudaStream_t s);
+// Single box: true when the apply should convert the sums itself (the MD
+// branch sets the step), false when the stream-collide sets it -- taken as a
+// stream-collide moving 480 MB or more per step (~70 us at the HBM rate, about
+// the MD branch of a 400-bead chain beside it): FP32 populations of 3.2 M
+// nodes or more.
+inline bool spread_take_in_apply(int storage, long long nodes) {
+  const long long bytes = 2LL * 19 * nodes * (storage == LBMD_STORE_F32 ? 4 : 2);
+  return bytes < 480000000LL;
+}
 // `take`: the owners' forces from their fixed-point sums (the sum ran with
 // records == false), else from the records.  `bump` (may be null):
 // status->step += 1 by one thread.

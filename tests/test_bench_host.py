@@ -22,6 +22,10 @@ def test_launches_per_step():
     # 16-bit storage: the apply converts the sums (one sum kernel)
     for st in ("f16", "bf16"):
         assert bench.launches_per_step(bench.workload(0, st, _Args())) == 5
+    # a small box: the MD branch sets the step, the apply converts the sums
+    a = _Args()
+    a.workload = "small"
+    assert bench.launches_per_step(bench.workload(0, "f32", a)) == 5
     a = _Args()
     a.workload = "solvent"
     assert bench.launches_per_step(bench.workload(0, "f32", a)) == 1
