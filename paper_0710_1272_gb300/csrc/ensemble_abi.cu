@@ -299,6 +299,17 @@ cudaError_t enqueue_ens_step(lbmd_ensemble *e, int cur) {
                                        e->own)) != cudaSuccess)
     return err;
   if (t[2] && (err = cudaEventRecord(t[2], e->own)) != cudaSuccess) return err;
+  if (!e->solvent_free) {
+    // the sum part of the spread once every MD group is done, still beside
+    // the stream-collide
+    for (int s = 1; s < e->nside; ++s) {
+      if ((err = cudaEventRecord(e->ev_join[s], e->side[s])) != cudaSuccess) return err;
+      if ((err = cudaStreamWaitEvent(e->side[0], e->ev_join[s], 0)) != cudaSuccess) return err;
+    }
+    if ((err = launch_ens_spread_accum(e->d_mem, e->d_beads, e->E.nb, live, e->side[0])) !=
+        cudaSuccess)
+      return err;
+  }
   for (int s = 0; s < e->nside; ++s) {
     if ((err = cudaEventRecord(e->ev_join[s], e->side[s])) != cudaSuccess) return err;
     if ((err = cudaStreamWaitEvent(e->own, e->ev_join[s], 0)) != cudaSuccess) return err;
@@ -486,10 +497,6 @@ int lbmd_ensemble_create(const lbmd_params *members, int32_t count, void *dev_wo
     EnsMember &M = e->hmem[m];
     memset(&M, 0, sizeof(M));
     M.a = e->inst[m].chain;
-    // the MD blocks of coupled chains sum the spread (beside the stream-collide):
-    // in shared memory, or for chains longer than its table with global atomics;
-    // without a solvent there are no spread buffers (and md_accum is 0)
-    if (M.a.sp_src != nullptr && M.a.md_accum != kSumShared) M.a.md_accum = kSumGlobal;
     M.a.f = nullptr;
     M.a.f_mode = kPopPull;
     M.ph = e->inst[m].phys;

@@ -82,15 +82,13 @@ Layout make_layout(const lbmd_params &p, bool single_box) {
   L.lam = take(Np * sizeof(float));
   L.status = take(sizeof(DevStatus));
   L.diag = take((size_t)std::max(p.diag_capacity, 0) * sizeof(DevDiag));
-  // a chain coupled to the solvent: the apply records of the 8 N transfer
-  // entries; unless an ensemble's MD block sums the chain in shared memory,
-  // also the spread owner of every node (4 bytes per node) and the
-  // fixed-point sums
+  // a chain coupled to the solvent: the spread owner of every node (4 bytes
+  // per node) and the fixed-point sums of the 8 N transfer entries; a single
+  // box also keeps the apply records of the entries
   const bool coupled = p.n_beads > 0 && !p.solvent_free;
-  const bool global_sum = coupled && (single_box || p.n_beads > kSumSharedMaxN);
-  L.owner = global_sum ? take((size_t)V * sizeof(int)) : 0;
-  L.acc = global_sum ? take(8 * Np * sizeof(SpreadAcc)) : 0;
-  L.sp_src = coupled ? take(8 * Np * sizeof(float4)) : 0;
+  L.owner = coupled ? take((size_t)V * sizeof(int)) : 0;
+  L.acc = coupled ? take(8 * Np * sizeof(SpreadAcc)) : 0;
+  L.sp_src = coupled && single_box ? take(8 * Np * sizeof(float4)) : 0;
   L.stage = single_box ? take(L.stage_floats * sizeof(float)) : 0;
   L.total = o;
   return L;
@@ -457,11 +455,9 @@ cudaError_t init_instance(const lbmd_params &p, const Layout &L, char *ws, cudaS
   a = ChainArgs{};
   const size_t ne = 8 * (size_t)std::max(p.n_beads, 1);
   if (L.sp_src) {
-    // apply records without a node (-1); the MD block sums the spread of
-    // chains that fit its shared table, two kernels that of longer ones
+    // apply records without a node (-1)
     a.sp_src = (float4 *)(ws + L.sp_src);
     UP(cudaMemsetAsync(a.sp_src, 0xff, ne * sizeof(float4), s), "memset");
-    a.md_accum = L.owner ? kSumKernels : kSumShared;
   }
   if (L.owner) {
     // spread owners at rest (every byte 0x7f = kOwnerFree), impulse sums zero

@@ -33,10 +33,9 @@ struct Layout {
 };
 
 // single_box: the layout of a single-box context (with the host read-out
-// staging buffer and the spread owner field); false: of an ensemble member
-// (the ensemble keeps one staging buffer for all its members, and its MD
-// blocks sum the spread of chains of up to kSumSharedMaxN beads in shared
-// memory, without an owner field).
+// staging buffer and the spread records); false: of an ensemble member (the
+// ensemble keeps one staging buffer for all its members, and its apply
+// converts the spread sums without records).
 Layout make_layout(const lbmd_params &p, bool single_box);
 // Floats of staging a box needs for chunked host read-outs.
 size_t stage_floats_for(const lbmd_params &p);

@@ -111,14 +111,12 @@ struct ChainArgs {
   int *sp_node;             // [8N] grid node of each transfer weight, -1 none
   float *sp_w;              // [8N] renormalised transfer weights
   int *owner;               // [V] per node: smallest transfer entry of this step
-                            // that hits it (kOwnerFree at rest); kSumKernels and
-                            // kSumGlobal only
+                            // that hits it (kOwnerFree at rest); null without
+                            // a solvent
   SpreadAcc *acc;           // [8N] impulse sums, at the owner entry of each node
-                            // (kSumKernels and kSumGlobal only)
   float4 *sp_src;           // [8N] apply records (F_x, F_y, F_z, node) of the
                             // transfer nodes, F the node's summed force; unused
-                            // records have node = -1
-  int md_accum;             // how the spread is summed (kSum*)
+                            // records have node = -1 (single box)
   const double *b0;         // [N-1] bond lengths
   int *nl_cnt, *wl_cnt;     // [N] list lengths
   short *nl_list;           // [N][kMaxPairs] partner beads
@@ -214,26 +212,18 @@ cudaError_t launch_md_cycle(const ChainArgs &a, int priority, cudaStream_t s);
 //  - sum (any time after the MD cycle; all contributions to a box come from
 //    its one chain): every entry adds its share -w J_i of the impulse to
 //    acc[owner] in 64-bit fixed point; then each owner converts its sum once
-//    into sp_src[owner] = (F, node), and returns acc and owner[node] to rest
-//    (kSumShared: the same sums in a shared-memory table, below);
+//    (into the record sp_src[owner] = (F, node), or in the apply itself) and
+//    returns acc and owner[node] to rest;
 //  - apply (after the stream-collide): each owner entry adds the source
 //    S_p = 3 w_p c_p . F to its node's post-collision populations of `dst` in
 //    layout `mode` -- the only write to those words.
-// launch_spread_sum enqueues the sum as two kernels, or only the first when
-// the apply converts the sums itself (records == false; chains whose MD block
-// sums instead have md_accum set).
-// A single box sums with the owner field and global atomics in two kernels
-// after the MD cycle (kSumKernels: spread over many SMs, whose global memory
-// traffic is fast even while the stream-collide saturates HBM).  In an
-// ensemble, whose MD blocks run beside a far longer stream-collide, each MD
-// block sums its own chain after its last substep: for chains of up to
-// kSumSharedMaxN beads in a hash table of the chain's transfer nodes kept in
-// its (then free) shared memory (kSumShared: 64-bit fixed-point shared
-// atomics, no owner field; the records sit at the table's slots), for longer
-// ones with the owner field and global atomics (kSumGlobal).
+// The sums run in kernels of their own after the MD cycle, spread over many
+// SMs (global atomics from one SM, in the MD block, were slow while the
+// stream-collide saturates HBM).  launch_spread_sum enqueues the sum as two
+// kernels, or only the first when the apply converts the sums itself
+// (records == false); an ensemble uses launch_ens_spread_accum and converts
+// in its apply.
 constexpr int kOwnerFree = 0x7f7f7f7f;
-constexpr int kSumKernels = 0, kSumGlobal = 1, kSumShared = 2;
-constexpr int kSumSharedMaxN = 512;
 cudaError_t launch_spread_sum(const ChainArgs &a, bool records, cudaStream_t s);
 // Single box: true when the apply should convert the sums itself (the MD
 // branch sets the step), false when the stream-collide sets it -- taken as a
@@ -275,8 +265,11 @@ cudaError_t launch_ens_gather(int storage, const EnsMember *mem, const int2 *bea
 // threads each, with dynamic shared memory for `max_n` beads.
 cudaError_t launch_ens_md_cycle(const EnsMember *mem, const int *chains, int count, int threads,
                                 int max_n, const int *live, int priority, cudaStream_t s);
-// Apply part of the spread (the MD blocks of an ensemble sum the impulses
-// themselves) into pop[1 - cur]; bumps each live realisation's step
+// Sum part of the spread of every live realisation (after every MD group).
+cudaError_t launch_ens_spread_accum(const EnsMember *mem, const int2 *beads, int nb,
+                                    const int *live, cudaStream_t s);
+// Apply part of the spread (the owners convert their sums) into pop[1 - cur];
+// bumps each live realisation's step
 // count and writes its flag for the next step into `live_next` (still running
 // and step < *max_steps).
 cudaError_t launch_ens_spread(int storage, const EnsMember *mem, const int2 *beads, int nb,

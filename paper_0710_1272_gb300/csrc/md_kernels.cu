@@ -592,64 +592,6 @@ __device__ __forceinline__ void spread_finalize(const ChainArgs &a, int e) {
   a.sp_src[e] = out;
 }
 
-// The spread sum of one chain in its MD block (kSumShared), after the last
-// substep: an open-addressing hash table of the chain's transfer nodes in the
-// block's dynamic shared memory (8 N slots: room for every entry), 64-bit
-// fixed-point shared atomics per node, then one record per slot.  Which slot a
-// node lands in depends on the order of the atomics; its sum does not.
-struct __align__(8) SpreadSlot {
-  int node, bad;
-  long long x, y, z;
-};
-
-__device__ __forceinline__ void spread_sum_shared(const ChainArgs &a, void *smem, bool bead, int i,
-                                                  F3 J) {
-  SpreadSlot *T = reinterpret_cast<SpreadSlot *>(smem);
-  const unsigned S = 8u * (unsigned)a.N;
-  __syncthreads();  // every read of the substep arrays is done
-  for (unsigned s = threadIdx.x; s < S; s += blockDim.x) T[s] = SpreadSlot{-1, 0, 0, 0, 0};
-  __syncthreads();
-  if (bead) {
-    int node[8];
-    float w[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      node[k] = a.sp_node[8 * i + k];
-      w[k] = a.sp_w[8 * i + k];
-    }
-    const float lim = 1024.0f;  // as spread_add: a larger share marks the sum
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (node[k] < 0) continue;
-      unsigned h = ((unsigned)node[k] * 2654435761u) % S;
-      for (;;) {  // at most S probes: the table has a slot for every entry
-        const int old = atomicCAS(&T[h].node, -1, node[k]);
-        if (old == -1 || old == node[k]) break;
-        h = h + 1 == S ? 0 : h + 1;
-      }
-      const float fx = -w[k] * J.x, fy = -w[k] * J.y, fz = -w[k] * J.z;
-      if (!(fabsf(fx) < lim && fabsf(fy) < lim && fabsf(fz) < lim)) {
-        atomicOr(&T[h].bad, 1);
-        continue;
-      }
-      atomicAdd(reinterpret_cast<unsigned long long *>(&T[h].x), (unsigned long long)fix40(fx));
-      atomicAdd(reinterpret_cast<unsigned long long *>(&T[h].y), (unsigned long long)fix40(fy));
-      atomicAdd(reinterpret_cast<unsigned long long *>(&T[h].z), (unsigned long long)fix40(fz));
-    }
-  }
-  __syncthreads();
-  for (unsigned s = threadIdx.x; s < S; s += blockDim.x) {
-    const SpreadSlot t = T[s];
-    float4 r = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-    if (t.node >= 0) {
-      const float nan = __int_as_float(0x7fc00000);
-      r = t.bad ? make_float4(nan, nan, nan, __int_as_float(t.node))
-                : make_float4(unfix40(t.x), unfix40(t.y), unfix40(t.z), __int_as_float(t.node));
-    }
-    a.sp_src[s] = r;
-  }
-}
-
 // (2) the M MD substeps of one chain, one thread per bead, and (5) the
 // bookkeeping; `a` may live in parameter or shared memory.
 template <bool WS>
@@ -851,20 +793,12 @@ __device__ __forceinline__ void md_cycle_body(const ChainArgs &a) {
     a.vel[i] = f4(v);
     a.J[i] = f4(J);
     a.lam[i] = s_lam[i];
-    if (a.md_accum == kSumGlobal)  // spread (3): the bead's 8 corner shares into the sums
-#pragma unroll
-      for (int k = 0; k < 8; ++k) spread_add(a, 8 * i + k, f4(J));
   }
-  if (a.md_accum == kSumShared) spread_sum_shared(a, smem4, bead, i, J);
   // Translocation bookkeeping (Sec. III): unwrapped x = origin + hi + lo
   const float xrel = bead ? ((float)(a.ox - a.wall_x) + rh.x) + rl.x : 0.f;
   const bool finite = isfinite(rh.x) && isfinite(rh.y) && isfinite(rh.z) && isfinite(v.x) &&
                       isfinite(v.y) && isfinite(v.z);
   const int nt = __syncthreads_count(bead && a.has_wall && xrel < 0.f);
-  // every share of this chain is summed (barrier above): the owners' records
-  if (a.md_accum == kSumGlobal && bead)
-#pragma unroll
-    for (int k = 0; k < 8; ++k) spread_finalize(a, 8 * i + k);
   const int nan = __syncthreads_or(bead && !finite);
   const int out = __syncthreads_and(!bead || xrel > (float)(a.wall_t - 1) + 1.5f);
   const int bad = __syncthreads_or(shake_bad);
@@ -1205,9 +1139,10 @@ cudaError_t launch_spread_apply(int storage, const LbGeom &g, const ChainArgs &a
   return cudaGetLastError();
 }
 
-// Ensemble apply: same lane layout as k_ens_gather (the MD blocks have
-// summed the impulses into the owners' records).  The first lane of every realisation bumps its
-// step count (if live) and decides whether it takes part in the next step.
+// Ensemble apply: same lane layout as k_ens_gather; each owner entry converts
+// its node's sum (k_ens_spread_accum) and adds the source as k_spread_apply
+// does.  The first lane of every realisation bumps its step count (if live)
+// and decides whether it takes part in the next step.
 template <int S>
 __global__ void __launch_bounds__(256)
     k_ens_spread(const EnsMember *__restrict__ mem, const int2 *__restrict__ beads, int nb,
@@ -1219,12 +1154,12 @@ __global__ void __launch_bounds__(256)
   int2 mi = make_int2(-1, 0);
   if (slot < nb) mi = beads[slot];
   const bool valid = mi.x >= 0 && live[mi.x];
-  if (valid && mem[mi.x].a.sp_src) {
-    const float4 v = mem[mi.x].a.sp_src[8 * mi.y + k];
-    const int node = __float_as_int(v.w);
-    if (node >= 0) {  // the owner's record
-      const F3 F{v.x, v.y, v.z};
-      const ChainArgs &a = mem[mi.x].a;
+  if (valid && mem[mi.x].a.owner) {
+    const ChainArgs &a = mem[mi.x].a;
+    const int e2 = 8 * mi.y + k;
+    const int node = a.sp_node[e2];
+    if (node >= 0 && a.owner[node] == e2) {  // the owner converts its node's sum
+      const F3 F = spread_take(a, node, e2);
       typename St::T *dst = (typename St::T *)mem[mi.x].pop[cur ^ 1];
       const size_t Vp = (size_t)a.geo.Vp;
       if (S == LBMD_STORE_F32) {
@@ -1283,6 +1218,29 @@ cudaError_t launch_ens_md_cycle(const EnsMember *mem, const int *chains, int cou
   cfg.numAttrs = 1;
   if (threads <= 512) return cudaLaunchKernelEx(&cfg, k_ens_md_cycle<512>, mem, chains, live);
   return cudaLaunchKernelEx(&cfg, k_ens_md_cycle<1024>, mem, chains, live);
+}
+
+// Ensemble sum part of the spread, after every MD group: one thread per
+// (realisation, bead, corner) entry as in k_ens_gather, adding the entry's
+// share to its owner's fixed-point sum (spread_add).
+__global__ void __launch_bounds__(256)
+    k_ens_spread_accum(const EnsMember *__restrict__ mem, const int2 *__restrict__ beads, int nb,
+                       const int *__restrict__ live) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int slot = e >> 3, k = e & 7;
+  if (slot >= nb) return;
+  const int2 mi = beads[slot];
+  if (mi.x < 0 || !live[mi.x]) return;
+  const ChainArgs &a = mem[mi.x].a;
+  if (a.owner == nullptr) return;  // no solvent: nothing to spread
+  spread_add(a, 8 * mi.y + k, a.J[mi.y]);
+}
+
+cudaError_t launch_ens_spread_accum(const EnsMember *mem, const int2 *beads, int nb,
+                                    const int *live, cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  k_ens_spread_accum<<<(8 * nb + 255) / 256, 256, 0, s>>>(mem, beads, nb, live);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ens_spread(int storage, const EnsMember *mem, const int2 *beads, int nb,
