@@ -237,17 +237,21 @@ typedef struct lbmd_status_word {
 
 /*
  * Asynchronous host read-out for pipelined loops: enqueues on the context's
- * stream one kernel and one copy that fill `dst` (caller-owned page-locked
- * host memory: cudaHostAlloc / cudaHostRegister) with
+ * stream one kernel that fills `dst` (caller-owned page-locked host memory:
+ * cudaHostAlloc / cudaHostRegister) -- writing it directly when the device
+ * can address it (cudaHostAlloc memory on a unified-addressing system,
+ * mapped registrations), else through the context's staging buffer and one
+ * copy -- with
  *   offset 0:            lbmd_status_word,
  *   offset 32:           unwrapped positions, 3*n_beads doubles [i][xyz],
  *   offset 32 + 24 n:    velocities, 3*n_beads doubles,
  * LBMD_BEAD_BLOCK_BYTES(n_beads) bytes in all.  Nothing is synchronised: the
  * block is valid once the stream has passed this point (synchronise it, or an
  * event recorded on it after this call).  A following lbmd_step may be
- * enqueued at once; its kernels run after the copy.  With pageable memory the
- * call may block until the copy is done.  Uses the context's read-out staging;
- * read-outs enqueued later on the stream do not disturb it.
+ * enqueued at once; its kernels run after the read-out.  With pageable memory
+ * the call may block until the copy is done.  The staging buffer is used
+ * only for a dst the device cannot address; read-outs enqueued later on the
+ * stream do not disturb it.
  * Errors: LBMD_EINVAL (dst NULL or bytes too small), LBMD_ECUDA.
  */
 int lbmd_read_beads_async(lbmd_ctx *ctx, void *dst, size_t bytes);

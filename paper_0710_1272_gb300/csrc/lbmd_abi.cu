@@ -458,7 +458,19 @@ int lbmd_read_beads_async(lbmd_ctx *c, void *dst, size_t bytes) {
   if (rc) return rc;
   const size_t need = kBeadBlockHeader + 48 * (size_t)c->N;
   if (!dst || bytes < need) return fail(LBMD_EINVAL, "dst is NULL or smaller than %zu bytes", need);
-  // one kernel fills the block in the staging buffer, one copy moves it
+  // page-locked memory the device can address (cudaHostAlloc, or registered
+  // as mapped): the kernel writes the block into it directly; otherwise it
+  // fills the staging buffer and one copy moves it
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, dst) != cudaSuccess) {
+    (void)cudaGetLastError();  // clear: the pointer is just not known to CUDA
+    at.type = cudaMemoryTypeUnregistered;
+    at.devicePointer = nullptr;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr) {
+    CK(c, launch_bead_block(c->chain, c->status, at.devicePointer, c->user));
+    return LBMD_OK;
+  }
   CK(c, launch_bead_block(c->chain, c->status, c->stage, c->user));
   CK(c, cudaMemcpyAsync(dst, c->stage, need, cudaMemcpyDeviceToHost, c->user));
   return LBMD_OK;

@@ -81,3 +81,24 @@ def test_async_readout_checks_size_and_works_without_beads():
     lb.lbmd_read_beads_async(sim.ctx, blk.data_ptr(), blk.numel())
     sim.stream.synchronize()
     assert lb.decode_bead_block(blk.numpy(), 0)[0]["step"] == 3
+
+
+def test_async_readout_into_pageable_memory():
+    """Memory the device cannot address takes the staging buffer and a copy;
+    the block is the same as the one written straight into pinned memory."""
+    torch, lb = _gpu()
+    p = si.small_translocation(2)
+    sim = lb.Simulation(p, init_pos=si.saw_chain(p, 2))
+    sim.step(7)
+    N = p["n_beads"]
+    pageable = np.zeros(lb.bead_block_bytes(N), dtype=np.uint8)
+    pinned = _block(torch, lb, N)
+    lb.lbmd_read_beads_async(sim.ctx, pageable.ctypes.data, pageable.nbytes)
+    lb.lbmd_read_beads_async(sim.ctx, pinned.data_ptr(), pinned.numel())
+    sim.stream.synchronize()
+    np.testing.assert_array_equal(pageable, pinned.numpy())
+    status, pos, vel = lb.decode_bead_block(pageable, N)
+    r, v = sim.beads()
+    assert status["step"] == 7
+    np.testing.assert_array_equal(pos, r)
+    np.testing.assert_array_equal(vel, v)
