@@ -337,9 +337,10 @@ def run_ours(args):
     st = sim.status()
 
     # -- end to end through the public API with host buffers ------------------
-    # Every step: lbmd_step(1), then lbmd_read_beads_async of its status word,
-    # positions and velocities into page-locked host memory (double-buffered);
-    # the host waits for step k's block after step k+1 is enqueued and checks it.
+    # Every step: lbmd_step_read_async -- one step and the read-out of its
+    # status word, positions and velocities into page-locked host memory
+    # (double-buffered); the host waits for step k's block after step k+1 is
+    # enqueued and checks it.
     e2e_steps = args.e2e_steps
     N = p["n_beads"]
     nbytes = lb.bead_block_bytes(N)
@@ -352,15 +353,15 @@ def run_ours(args):
         status, pos_k, _ = lb.decode_bead_block(blocks[k % 2].numpy(), N)
         assert status["step"] == step0 + k + 1 and np.isfinite(pos_k).all()
 
-    # the one-step graphs of both step parities exist before the timed loop
-    lb.lbmd_step(sim.ctx, 1)
-    lb.lbmd_step(sim.ctx, 1)
+    # the step-and-read-out graphs of both step parities exist before the
+    # timed loop
+    for k in range(2):
+        lb.lbmd_step_read_async(sim.ctx, blocks[k].data_ptr(), nbytes)
     step0 += 2
     barrier()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        lb.lbmd_step(sim.ctx, 1)
-        lb.lbmd_read_beads_async(sim.ctx, blocks[k % 2].data_ptr(), nbytes)
+        lb.lbmd_step_read_async(sim.ctx, blocks[k % 2].data_ptr(), nbytes)
         evs[k % 2].record(stream)
         if k > 0:
             consume(k - 1)
@@ -434,7 +435,8 @@ def run_ours(args):
                 # 24-byte status word
                 "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": nbytes,
-                "api": ("lbmd_step(1) + lbmd_read_beads_async(pinned host block, double-buffered; "
+                "api": ("lbmd_step_read_async (one graph launch of the step and the kernel that "
+                        "writes its bead block into a pinned host block, double-buffered; "
                         "the host waits for and checks step k's block after enqueuing step k+1); "
                         "the state stays resident on the GPU between steps, so no host-to-device "
                         "copy per step; the field read-outs (lbmd_read_fields, "

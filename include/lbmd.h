@@ -257,6 +257,18 @@ typedef struct lbmd_status_word {
 int lbmd_read_beads_async(lbmd_ctx *ctx, void *dst, size_t bytes);
 
 /*
+ * One coupled step (Sec. II: interpolate, M MD substeps, spread, stream and
+ * collide; Sec. III bookkeeping) and the read-out of its bead block, as
+ * lbmd_step(ctx, 1) followed by lbmd_read_beads_async(ctx, dst, bytes) -- same
+ * block layout, same asynchrony, same requirements on dst -- but as one graph
+ * launch when the device can address dst: the read-out kernel is a node of
+ * the step's graph, and its destination is set before each launch.  For other
+ * memory, and while kernel timing is on, it makes the two calls.
+ * Errors: LBMD_EINVAL (dst NULL or bytes too small), LBMD_ECUDA.
+ */
+int lbmd_step_read_async(lbmd_ctx *ctx, void *dst, size_t bytes);
+
+/*
  * Of the last step: the fluid velocity interpolated at each bead, u_i, and the
  * impulse J_i = sum over substeps of Delta t_MD (F_drag + F_r) that was handed
  * to the fluid (with the opposite sign).  3*n_beads doubles each.

@@ -11,7 +11,7 @@ from .lbmd import (  # noqa: F401
     TRANSLOCATED, Ensemble, LbmdError, Simulation, bead_block_bytes, decode_bead_block,
     full_params, lbmd_create, lbmd_destroy,
     lbmd_kernel_times, lbmd_lb_kernel_time, lbmd_lb_step_noalloc, lbmd_read_bead_aux,
-    lbmd_read_beads, lbmd_read_beads_async, lbmd_read_fields, lbmd_read_populations,
+    lbmd_read_beads, lbmd_read_beads_async, lbmd_step_read_async, lbmd_read_fields, lbmd_read_populations,
     lbmd_set_kernel_timing, lbmd_solver_stats, lbmd_status, lbmd_status_word, lbmd_step,
     lbmd_version, lbmd_workspace_size, load, make_params,
 )

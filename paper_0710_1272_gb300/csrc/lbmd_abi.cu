@@ -35,6 +35,12 @@ struct lbmd_ctx {
   int prio_high;            // greatest stream priority of the device
   cudaEvent_t ev_in, ev_out, ev_fork, ev_join;
   cudaGraphExec_t graph[2][3];  // [starting buffer][1, 2, kBlockSteps steps]
+  // one step followed by the bead-block read-out, per starting buffer
+  // (lbmd_step_read_async); the read-out node's destination is set per launch
+  cudaGraph_t rtmpl[2];
+  cudaGraphExec_t rgraph[2];
+  cudaGraphNode_t rnode[2];
+  cudaKernelNodeParams rparams[2];
   int sticky;
   int timing;
   std::vector<cudaEvent_t> tev;  // per timed step: lb, md, spread start/stop pairs
@@ -187,12 +193,59 @@ cudaError_t capture(lbmd_ctx *c, int start, int nsteps, cudaGraphExec_t *out) {
   return e;
 }
 
+// One step from buffer `start` and the bead-block read-out after it, as one
+// graph; the read-out kernel's node (its destination is a placeholder, set
+// before every launch) is kept with the graph it belongs to.
+cudaError_t capture_read(lbmd_ctx *c, int start) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->own, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t e2 = enqueue_step(c, start);
+  if (e2 == cudaSuccess) e2 = launch_bead_block(c->chain, c->status, c->stage, c->own);
+  e = cudaStreamEndCapture(c->own, &g);
+  if (e2 == cudaSuccess) e2 = e;
+  size_t n = 0;
+  if (e2 == cudaSuccess) e2 = cudaGraphGetNodes(g, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (e2 == cudaSuccess && n > 0) e2 = cudaGraphGetNodes(g, nodes.data(), &n);
+  cudaGraphNode_t found = nullptr;
+  cudaKernelNodeParams kp = {};
+  for (size_t k = 0; k < n && e2 == cudaSuccess && !found; ++k) {
+    cudaGraphNodeType ty;
+    if ((e2 = cudaGraphNodeGetType(nodes[k], &ty)) != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams q = {};
+    if ((e2 = cudaGraphKernelNodeGetParams(nodes[k], &q)) != cudaSuccess) break;
+    if (q.func == bead_block_kernel()) {
+      found = nodes[k];
+      kp = q;
+    }
+  }
+  if (e2 == cudaSuccess && !found) e2 = cudaErrorInvalidValue;
+  cudaGraphExec_t ex = nullptr;
+  if (e2 == cudaSuccess) e2 = cudaGraphInstantiate(&ex, g, cudaGraphInstantiateFlagUseNodePriority);
+  if (e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return e2;
+  }
+  c->rtmpl[start] = g;
+  c->rgraph[start] = ex;
+  c->rnode[start] = found;
+  kp.kernelParams = nullptr;  // rebuilt per launch
+  kp.extra = nullptr;
+  c->rparams[start] = kp;
+  return cudaSuccess;
+}
+
 void destroy_ctx(lbmd_ctx *c) {
   if (!c) return;
   for (auto &row : c->graph)
     for (auto &gx : row)
       if (gx) cudaGraphExecDestroy(gx);
   for (cudaGraphExec_t ex : c->tgraphs) cudaGraphExecDestroy(ex);
+  for (int k = 0; k < 2; ++k) {
+    if (c->rgraph[k]) cudaGraphExecDestroy(c->rgraph[k]);
+    if (c->rtmpl[k]) cudaGraphDestroy(c->rtmpl[k]);
+  }
   for (cudaEvent_t ev : c->tev) cudaEventDestroy(ev);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
@@ -339,6 +392,40 @@ int lbmd_step(lbmd_ctx *c, int64_t n_steps) {
       left -= len;
     }
   }
+  return LBMD_OK;
+}
+
+int lbmd_step_read_async(lbmd_ctx *c, void *dst, size_t bytes) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  const size_t need = kBeadBlockHeader + 48 * (size_t)c->N;
+  if (!dst || bytes < need) return fail(LBMD_EINVAL, "dst is NULL or smaller than %zu bytes", need);
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, dst) != cudaSuccess) {
+    (void)cudaGetLastError();  // clear: the pointer is just not known to CUDA
+    at.type = cudaMemoryTypeUnregistered;
+    at.devicePointer = nullptr;
+  }
+  if (c->timing || at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) {
+    // the two calls it stands for (timed steps, or memory the device cannot
+    // address: the staged copy)
+    if ((rc = lbmd_step(c, 1))) return rc;
+    return lbmd_read_beads_async(c, dst, bytes);
+  }
+  const int k = c->cur;
+  if (!c->rgraph[k]) CK(c, capture_read(c, k));
+  const ChainArgs &a = c->chain;
+  const float4 *pos = a.pos, *pos_lo = a.pos_lo, *vel = a.vel;
+  int N = a.N, ox = a.ox, oy = a.oy, oz = a.oz;
+  const DevStatus *st = c->status;
+  char *out = (char *)at.devicePointer;
+  void *args[9] = {&pos, &pos_lo, &vel, &N, &ox, &oy, &oz, &st, &out};
+  cudaKernelNodeParams kp = c->rparams[k];
+  kp.kernelParams = args;
+  CK(c, cudaGraphExecKernelNodeSetParams(c->rgraph[k], c->rnode[k], &kp));
+  CK(c, cudaGraphLaunch(c->rgraph[k], c->user));
+  c->cur ^= 1;
+  c->status_fresh = 0;
   return LBMD_OK;
 }
 

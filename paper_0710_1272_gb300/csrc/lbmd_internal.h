@@ -281,6 +281,9 @@ cudaError_t launch_read_beads(const float4 *pos, const float4 *pos_lo, const flo
 // The block of lbmd_read_beads_async into device memory `out` (32 + 48 N bytes).
 constexpr size_t kBeadBlockHeader = 32;
 cudaError_t launch_bead_block(const ChainArgs &a, const DevStatus *st, void *out, cudaStream_t s);
+// The kernel launch_bead_block launches (to find its node in a captured graph;
+// its arguments: pos, pos_lo, vel, N, ox, oy, oz, status, out).
+const void *bead_block_kernel();
 cudaError_t launch_read_bead_aux(const float4 *ui, const float4 *J, int N, double *dui,
                                  double *dJ, cudaStream_t s);
 

@@ -1294,6 +1294,8 @@ __global__ void k_bead_block(const float4 *pos, const float4 *pos_lo, const floa
     w->n_trans = st->n_trans;
     // a box without beads has no apply kernel to fold the population flag in
     w->state = st->state == LBMD_RUNNING && st->pop_bad ? LBMD_NAN : st->state;
+    // the header's padding reads zero: every byte of the block is defined
+    for (size_t b = sizeof(lbmd_status_word); b < kBeadBlockHeader; b += sizeof(int)) *(int *)(out + b) = 0;
   }
   if (i >= N) return;
   double *dpos = (double *)(out + kBeadBlockHeader), *dvel = dpos + 3 * (size_t)N;
@@ -1305,6 +1307,8 @@ __global__ void k_bead_block(const float4 *pos, const float4 *pos_lo, const floa
   dvel[3 * i + 1] = v.y;
   dvel[3 * i + 2] = v.z;
 }
+
+const void *bead_block_kernel() { return reinterpret_cast<const void *>(&k_bead_block); }
 
 cudaError_t launch_bead_block(const ChainArgs &a, const DevStatus *st, void *out, cudaStream_t s) {
   const int n = a.N > 0 ? a.N : 1;

@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True):
     L.lbmd_read_beads.argtypes = [P, P, P, C.c_int]
     L.lbmd_read_bead_aux.argtypes = [P, P, P, C.c_int]
     L.lbmd_read_beads_async.argtypes = [P, P, C.c_size_t]
+    L.lbmd_step_read_async.argtypes = [P, P, C.c_size_t]
     L.lbmd_status.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                               C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
     L.lbmd_solver_stats.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
@@ -145,7 +146,7 @@ def load(build_if_missing: bool = True):
     L.lbmd_last_message.restype = C.c_char_p
     for name in ("lbmd_workspace_size", "lbmd_create", "lbmd_step", "lbmd_read_fields",
                  "lbmd_read_populations", "lbmd_read_beads", "lbmd_read_bead_aux", "lbmd_status",
-                 "lbmd_read_beads_async",
+                 "lbmd_read_beads_async", "lbmd_step_read_async",
                  "lbmd_set_kernel_timing", "lbmd_lb_kernel_time", "lbmd_destroy", "lbmd_version",
                  "lbmd_solver_stats", "lbmd_kernel_times", "lbmd_lb_step_noalloc",
                  "lbmd_read_diagnostics", "lbmd_ensemble_read_diagnostics", *ENSEMBLE_FUNCTIONS):
@@ -249,6 +250,13 @@ def lbmd_read_beads(ctx, pos_ptr, vel_ptr, dst_is_device: int) -> None:
 def bead_block_bytes(n_beads: int) -> int:
     """Bytes of the block lbmd_read_beads_async writes (LBMD_BEAD_BLOCK_BYTES)."""
     return 32 + 48 * int(n_beads)
+
+
+def lbmd_step_read_async(ctx, dst_ptr, nbytes: int) -> None:
+    """One coupled step and the read-out of its bead block into ``dst_ptr``
+    (as lbmd_step(ctx, 1) + lbmd_read_beads_async, one graph launch for
+    page-locked memory the device can address)."""
+    _check(load().lbmd_step_read_async(ctx, dst_ptr, int(nbytes)), "lbmd_step_read_async")
 
 
 def lbmd_read_beads_async(ctx, dst_ptr, nbytes: int) -> None:

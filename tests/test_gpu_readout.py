@@ -102,3 +102,41 @@ def test_async_readout_into_pageable_memory():
     assert status["step"] == 7
     np.testing.assert_array_equal(pos, r)
     np.testing.assert_array_equal(vel, v)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_step_read_async_equals_step_then_read(pinned):
+    """lbmd_step_read_async (one graph of the step and its read-out, or the
+    two separate calls for memory the device cannot address) delivers, block
+    for block, what lbmd_step(1) + lbmd_read_beads_async deliver, also
+    double-buffered behind the following steps and across both buffers."""
+    torch, lb = _gpu()
+    p = si.small_translocation(3)
+    pos0 = si.saw_chain(p, 3)
+    a = lb.Simulation(p, init_pos=pos0)
+    b = lb.Simulation(p, init_pos=pos0)
+    N = p["n_beads"]
+    if pinned:
+        blocks = [_block(torch, lb, N) for _ in range(2)]
+        view = [blk.numpy() for blk in blocks]
+        ptr = [blk.data_ptr() for blk in blocks]
+    else:
+        view = [np.zeros(lb.bead_block_bytes(N), dtype=np.uint8) for _ in range(2)]
+        ptr = [v.ctypes.data for v in view]
+    ref = _block(torch, lb, N)
+    events = [torch.cuda.Event(), torch.cuda.Event()]
+    for k in range(7):
+        lb.lbmd_step_read_async(a.ctx, ptr[k % 2], len(view[k % 2]))
+        events[k % 2].record(a.stream)
+        lb.lbmd_step(b.ctx, 1)
+        lb.lbmd_read_beads_async(b.ctx, ref.data_ptr(), ref.numel())
+        b.stream.synchronize()
+        events[k % 2].synchronize()
+        np.testing.assert_array_equal(view[k % 2], ref.numpy())
+        assert lb.decode_bead_block(view[k % 2], N)[0]["step"] == k + 1
+    # the graphs of both buffers and the plain path interleave
+    a.step(3)
+    b.step(3)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    with pytest.raises(lb.LbmdError):
+        lb.lbmd_step_read_async(a.ctx, ptr[0], 16)
