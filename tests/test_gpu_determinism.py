@@ -92,6 +92,27 @@ def test_benchmark_box_bit_identical():
     assert sa == b.status()
 
 
+def test_benchmark_box_records_and_apply_conversion_agree():
+    """The FP32 benchmark box converts the spread sums in k_spread_finalize
+    (its stream-collide sets the step); an ensemble converts them in its apply
+    kernel.  Both convert the same fixed-point sums once per node: the same
+    box as a one-member ensemble holds the single box's bits."""
+    lb = _lb()
+    p = si.paper_translocation(0)
+    pos = si.saw_chain(p, 0)
+    a = lb.Simulation(p, init_pos=pos)
+    a.step(40)
+    fa = a.populations()
+    ra, va = a.beads()
+    a.close()
+    ens = lb.Ensemble([p], [pos])
+    ens.step(40)
+    np.testing.assert_array_equal(ens.populations(0), fa)
+    re, ve = ens.beads(0)
+    np.testing.assert_array_equal(re, ra)
+    np.testing.assert_array_equal(ve, va)
+
+
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 def test_ensemble_1000_steps_bit_identical(storage):
     lb = _lb()
