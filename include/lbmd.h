@@ -180,7 +180,11 @@ int lbmd_workspace_size(const lbmd_params *params, size_t *bytes);
  * optional y-walls), the equilibrium populations f = f_eq(rho, u) of the
  * initial fields, and the bead state; everything is written into the caller's
  * workspace on `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
- * The call synchronises the stream before it returns.
+ * The call synchronises the stream before it returns.  With beads it marks
+ * the chain's buffers (about 1 MB for 400 beads) as an L2-persisting access
+ * window for the context's own kernels, raising the CUDA context's
+ * persisting-L2 limit (cudaLimitPersistingL2CacheSize) to that size if it is
+ * lower; nothing else of the device's state is changed.
  * Errors: LBMD_EINVAL, LBMD_ESIZE (bytes too small or workspace not 256-byte
  * aligned), LBMD_EUNSUPPORTED (constraint topology other than a linear
  * chain), LBMD_ECUDA.  On error *out is NULL and nothing is leaked.
