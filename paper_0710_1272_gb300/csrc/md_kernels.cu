@@ -566,8 +566,7 @@ __device__ __forceinline__ void spread_add(const ChainArgs &a, int e, float4 j) 
 
 // The owner's conversion: the summed force of node `node` (NaN if a
 // contribution was not finite); the sum and the node's owner return to rest.
-// The sum is read through L2: within an MD block it was written by other
-// threads' atomics before a barrier.
+// The sum is read through L2 (it was written by atomics of an earlier kernel).
 __device__ __forceinline__ F3 spread_take(const ChainArgs &a, int node, int e) {
   SpreadAcc *q = a.acc + e;
   const long long x = __ldcg(&q->x), y = __ldcg(&q->y), z = __ldcg(&q->z), bad = __ldcg(&q->bad);
