@@ -232,11 +232,10 @@ def test_ensemble_xpair_needs_16_bit_storage():
         ens.set_tuning(8, 32, 2, lb.ENS_XPAIR)
 
 
-def test_ensemble_long_chain_global_sum_matches_single_box():
-    """A chain longer than the MD block's shared spread table (600 beads)
-    sums its spread with global atomics in the ensemble's MD epilogue and
-    with two kernels in the single box; both give the same bits, beside a
-    short chain summed in shared memory."""
+def test_ensemble_long_chain_matches_single_box():
+    """A 600-bead chain (the 1024-thread MD block) beside a 20-bead one: the
+    ensemble's spread sum kernel over both chains and the apply's conversion
+    give the same bits as the single boxes."""
     lb = _lb()
     members = [si.ragged_member(600, 5, seed=61, lj_eps=PAPER_EPS),
                si.ragged_member(20, 3, seed=62, lj_eps=PAPER_EPS)]
